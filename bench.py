@@ -1,0 +1,639 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the Squares generator (arXiv:2004.06278) on GB300.
+
+One step = one pass of the hot path over the single-stream throughput
+workload: squares64 into uint64[2^30] (8 GiB) and squares32 into
+uint32[2^32] (16 GiB), one key (first key of seed 2), counter base drawn
+uniformly from [0, 2^64) (seed 3). With N ranks each rank generates the same
+amount from its own disjoint counter range (weak scaling; no collective on
+the data path -- the only collectives are the timing barrier and the max of
+the elapsed times).
+
+Printed: one JSON line with value = whole-job Gsamples/s (device-resident
+outputs), the roofline of the dominant kernel (squares32), the oracle timed
+on the host cores, the end-to-end rate with outputs copied into pinned host
+memory, the SM clocks sampled during the timed region, and a breakdown of
+the other kernels (ragged batch vs plain, transforms, fused statistics,
+cuRAND Philox4x32-10 as context), each measured outside the timed region.
+
+--impl reference times the oracle (plain C on the host cores) on a bounded
+sample of the same workload and prints the same metric with
+"impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gsamples/s squares32/64, batched vs plain, % of IMAD/HBM-store roofline"
+N64 = 1 << 30
+N32 = 1 << 32
+WORKLOAD = ("squares64 -> uint64[2^30] + squares32 -> uint32[2^32], one key (sq_make_keys seed 2), "
+            "counter base uniform in [0,2^64) (seed 3)")
+# Work per squares32 sample: 4 rounds, each one 32x32->64 multiply-add (two
+# issue slots of the integer multiply pipe) and one 32-bit multiply-add.
+IMAD_SLOTS_SQ32 = 12
+IMAD_SLOTS_SQ64 = 15
+IMAD_LANES_PER_SM_CLK = 64
+
+
+def parse_args():
+    p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-extras", action="store_true", help="skip the breakdown section")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-tune", action="store_true", help="use the default launch table")
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--profile", choices=["u32", "u64", "batch", "uniform_f32", "uniform_bf16",
+                                         "normal_f32", "fused"],
+                   help="run one kernel on a small case (for ncu) instead of the benchmark")
+    p.add_argument("--profile-n", type=int, default=1 << 28)
+    return p.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="sq_clocks_", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.dev), "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(power) if power else None}
+
+
+# --------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+
+def oracle_sample_rate(n64: int, n32: int, chunk: int = 1 << 26):
+    """Time the oracle (as it stands) on n64 squares64 and n32 squares32
+    samples, in chunks; returns (samples/s, seconds, threads)."""
+    import oracle
+
+    key = int(oracle.make_keys(2, 1)[0])
+    from paper_2004_06278_gb300 import workloads
+
+    base = workloads.throughput_base(3)
+    threads = oracle.default_threads()
+    oracle.fill32(key, base, 1 << 16)  # load the library outside the timing
+    t0 = time.perf_counter()
+    for a in range(0, n64, chunk):
+        oracle.fill64(key, (base + a) % (1 << 64), min(chunk, n64 - a), threads=threads)
+    for a in range(0, n32, chunk):
+        oracle.fill32(key, (base + a) % (1 << 64), min(chunk, n32 - a), threads=threads)
+    dt = time.perf_counter() - t0
+    return (n64 + n32) / dt, dt, threads
+
+
+CPU_SAMPLE = (1 << 28, 1 << 30)  # squares64, squares32 samples: 1/4 of a step
+
+
+def cpu_baseline_block():
+    rate, dt, threads = oracle_sample_rate(*CPU_SAMPLE)
+    return {"value": rate / 1e9, "unit": "Gsamples/s", "cores": threads, "kind": "oracle",
+            "sample": f"2^28 squares64 + 2^30 squares32 samples of the step's workload "
+                      f"(1/4 of a step), oracle in 2^26-sample calls on {threads} threads, "
+                      f"{dt:.2f} s wall"}
+
+
+def reference_arm(args, rank, world):
+    """The oracle timed as it stands on the host cores. Each step is a
+    bounded sample of the workload (same 1:4 mix of squares64 and squares32
+    samples), sized from a calibration run so that all K steps take about a
+    minute."""
+    if rank != 0:
+        return 0
+    rate, _, threads = oracle_sample_rate(1 << 24, 1 << 26)  # calibration / warm-up
+    budget_s = 60.0
+    per_step = rate * budget_s / max(1, args.steps)
+    unit = 5 << 20  # 2^20 squares64 + 2^22 squares32
+    units = int(max(1, min((N64 + N32) // unit, per_step // unit)))
+    n64, n32 = units << 20, units << 22
+    times = []
+    for _ in range(args.steps):
+        _, dt, threads = oracle_sample_rate(n64, n32)
+        times.append(dt)
+    total = sum(times)
+    value = args.steps * (n64 + n32) / total / 1e9
+    sample = f"{n64} squares64 + {n32} squares32 samples per step of the GPU step's workload"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gsamples/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_per_step": sample,
+                   "parallelism": f"{threads} host threads"},
+        "cpu_baseline": {"value": value, "unit": "Gsamples/s", "cores": threads, "kind": "oracle",
+                         "sample": sample + "; plain-C oracle in 2^26-sample calls"},
+        "e2e": {"value": value, "unit": "Gsamples/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# our arm
+
+def source_hash(*rel):
+    h = hashlib.sha256()
+    for r in rel:
+        with open(os.path.join(ROOT, r), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+KERNEL_SOURCES = ("paper_2004_06278_gb300/csrc/kernels_plain.cu",
+                  "paper_2004_06278_gb300/csrc/squares_core.cuh")
+
+
+def profiled_traffic(name: str):
+    """DRAM bytes per launch recorded by ncu for `name`, if the profile was
+    taken on the current kernel source (same hash), else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    cur = source_hash(*KERNEL_SOURCES)
+    with open(path) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) >= 3 and parts[0] == name and parts[2] == cur:
+                return int(parts[1])
+    return None
+
+
+class Timer:
+    def __init__(self, torch, stream):
+        self.torch = torch
+        self.stream = stream
+        self.pairs = []
+
+    def span(self):
+        a = self.torch.cuda.Event(enable_timing=True)
+        b = self.torch.cuda.Event(enable_timing=True)
+        self.pairs.append((a, b))
+        return a, b
+
+    def mean_ms(self):
+        return sum(a.elapsed_time(b) for a, b in self.pairs) / max(1, len(self.pairs))
+
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    import paper_2004_06278_gb300 as sq
+    from paper_2004_06278_gb300 import _lib as C
+    from paper_2004_06278_gb300 import workloads
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sq.load()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    stream = torch.cuda.current_stream()
+    sh = int(stream.cuda_stream)
+    key = int(sq.make_keys(2, 1)[0])
+    base = (workloads.throughput_base(3) + rank * (1 << 32)) % (1 << 64)
+    out64 = torch.empty(N64, dtype=torch.int64, device=dev)
+    out32 = torch.empty(N32, dtype=torch.int32, device=dev)
+    if not args.no_tune:
+        C.sq_autotune(C.SQ_KERNEL_U64, N64)
+        C.sq_autotune(C.SQ_KERNEL_U32, N32)
+    cfg32 = C.sq_get_config(C.SQ_KERNEL_U32, N32)
+    cfg64 = C.sq_get_config(C.SQ_KERNEL_U64, N64)
+
+    t64 = Timer(torch, stream)
+    t32 = Timer(torch, stream)
+
+    def step(timed: bool):
+        if timed:
+            a, b = t64.span()
+            a.record(stream)
+        C.sq_u64(key, base, N64, out64.data_ptr(), sh)
+        if timed:
+            b.record(stream)
+            a, b = t32.span()
+            a.record(stream)
+        C.sq_u32(key, base, N32, out32.data_ptr(), sh)
+        if timed:
+            b.record(stream)
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    if rank == 0:
+        clocks.start()
+        time.sleep(0.3)  # let nvidia-smi start sampling
+    barrier()
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(args.steps):
+        step(True)
+    end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clock_info = clocks.stop() if rank == 0 else None
+    elapsed = start.elapsed_time(end) / 1000.0
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    samples = world * args.steps * (N64 + N32)
+    value = samples / elapsed / 1e9
+    ms32 = t32.mean_ms()
+    ms64 = t64.mean_ms()
+
+    result = None
+    if rank == 0:
+        peaks, peak_src = measured_peaks()
+        props = torch.cuda.get_device_properties(dev)
+        sms = props.multi_processor_count
+        sm_max = float(clock_info.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0))
+        int_peak_ops = sms * IMAD_LANES_PER_SM_CLK * sm_max * 1e6  # IMAD lane-slots per second
+        r32 = N32 / (ms32 / 1e3)
+        r64 = N64 / (ms64 / 1e3)
+        hbm = float(peaks["hbm_gbs"])
+        r_hbm32 = hbm * 1e9 / 4
+        r_int32 = int_peak_ops / IMAD_SLOTS_SQ32
+        if r_int32 < r_hbm32:
+            roof = {"bound": "alu", "achieved": r32 * IMAD_SLOTS_SQ32 / 1e12,
+                    "peak": int_peak_ops / 1e12, "unit": "Tops/s",
+                    "frac": r32 / r_int32}
+        else:
+            roof = {"bound": "hbm", "achieved": r32 * 4 / 1e9, "peak": hbm, "unit": "GB/s",
+                    "frac": r32 / r_hbm32}
+        roof.update({
+            "kernel": "sq_u32 (plain squares32, 2^32 outputs per launch)",
+            "traffic": profiled_traffic("sq_u32_plain"),
+            "algorithmic_bytes": 4 * N32,
+            "avg_launch_ms": ms32,
+            "peak_source": f"{peak_src}: hbm {hbm} GB/s (MEASURED_PEAKS.json); integer: "
+                           f"{sms} SMs x {IMAD_LANES_PER_SM_CLK} IMAD lanes/clk x {sm_max} MHz",
+            "frac_hbm": (r32 * 4 / 1e9) / hbm,
+            "frac_int": r32 / r_int32,
+            "squares64": {"avg_launch_ms": ms64, "GBps": r64 * 8 / 1e9,
+                          "frac_hbm": (r64 * 8 / 1e9) / hbm,
+                          "frac_int": r64 / (int_peak_ops / IMAD_SLOTS_SQ64)},
+        })
+        result = {
+            "metric": METRIC, "value": value, "unit": "Gsamples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed * 1000 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "samples_per_step_per_gpu": N64 + N32,
+                       "bytes_written_per_step_per_gpu": 8 * N64 + 4 * N32,
+                       "l2": "outputs (24 GiB per step) exceed the 129 MB L2; no flush",
+                       "parallelism": f"{world} rank(s), disjoint counter ranges, no collective",
+                       "launch": {"sq_u32": [C.sq_variant_name(0, cfg32.variant), cfg32.block,
+                                             cfg32.ctas_per_sm],
+                                  "sq_u64": [C.sq_variant_name(1, cfg64.variant), cfg64.block,
+                                             cfg64.ctas_per_sm],
+                                  "tuned": not args.no_tune}},
+            "roofline": roof,
+            "clocks": clock_info,
+            "gpu_launches": 2 * args.steps,
+        }
+    del out64, out32
+    torch.cuda.empty_cache()
+
+    if rank == 0 and not args.no_e2e:
+        result["e2e"] = e2e_block(torch, C, key, base, dev, args.e2e_steps)
+    if rank == 0 and not args.no_extras:
+        result["breakdown"] = breakdown(torch, sq, C, workloads, dev, ms32)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline_block()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def e2e_block(torch, C, key, base, dev, steps):
+    """Same step through the C ABI with the outputs landing in pinned host
+    memory: per chunk, the kernel writes a device staging buffer and a
+    cudaMemcpyAsync moves it to the host; two streams alternate so copies
+    overlap generation. The step's inputs are two 64-bit scalars passed by
+    value in the launch (no host-to-device copy)."""
+    chunk = 1 << 28  # elements
+    host64 = torch.empty(N64, dtype=torch.int64, pin_memory=True)
+    host32 = torch.empty(N32, dtype=torch.int32, pin_memory=True)
+    streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
+    stage = [torch.empty(chunk * 8, dtype=torch.uint8, device=dev) for _ in streams]
+
+    def run_step():
+        k = 0
+        for fn, host, n, es in ((C.sq_u64, host64, N64, 8), (C.sq_u32, host32, N32, 4)):
+            for a in range(0, n, chunk):
+                m = min(chunk, n - a)
+                s = streams[k % 2]
+                buf = stage[k % 2]
+                with torch.cuda.stream(s):
+                    fn(key, (base + a) % (1 << 64), m, buf.data_ptr(), int(s.cuda_stream))
+                    dst = host.view(torch.uint8)[a * es:(a + m) * es]
+                    dst.copy_(buf[:m * es], non_blocking=True)
+                k += 1
+        for s in streams:
+            s.synchronize()
+
+    run_step()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        run_step()
+    dt = (time.perf_counter() - t0) / steps
+    d2h = 8 * N64 + 4 * N32
+    res = {"value": (N64 + N32) / dt / 1e9, "unit": "Gsamples/s", "h2d_bytes_per_step": 0,
+           "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1000, "steps": steps,
+           "d2h_GBps": d2h / dt / 1e9,
+           "path": "sq_u64 / sq_u32 into 2 GiB device chunks, cudaMemcpyAsync to pinned host, "
+                   "2 streams overlapping"}
+    del host64, host32, stage
+    return res
+
+
+def _time_graph(torch, fn, reps, stream):
+    """Capture fn() into a CUDA graph on `stream`; mean ms per replay."""
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        fn()
+        stream.synchronize()
+        with torch.cuda.graph(g, stream=stream):
+            fn()
+    g.replay()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        g.replay()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def _time_launches(torch, fn, reps, stream):
+    with torch.cuda.stream(stream):
+        fn()
+        fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(reps):
+            fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def breakdown(torch, sq, C, workloads, dev, ms32_plain):
+    import numpy as np
+
+    out = {}
+    stream = torch.cuda.Stream(dev)
+    sh = lambda: int(stream.cuda_stream)  # noqa: E731
+    plain_rate = N32 / (ms32_plain / 1e3)
+    out["squares32_plain"] = {"Gsamples_per_s": plain_rate / 1e9, "GBps": plain_rate * 4 / 1e9}
+
+    # ragged batch, 4096 streams, one persistent launch replayed from a CUDA graph
+    b = workloads.ragged_batch(4096, seed=7)
+    keys = torch.from_numpy(sq.make_keys(b.key_seed, b.nstreams).view(np.int64)).to(dev)
+    bases = torch.from_numpy(b.bases.view(np.int64)).to(dev)
+    lengths = torch.from_numpy(b.lengths).to(dev)
+    offsets = torch.from_numpy(b.offsets).to(dev)
+    outb = torch.empty(b.total, dtype=torch.int32, device=dev)
+    C.sq_autotune(C.SQ_KERNEL_BATCH, b.total)
+    cfgb = C.sq_get_config(C.SQ_KERNEL_BATCH, 0)
+
+    def run_batch():
+        C.sq_batch(keys.data_ptr(), bases.data_ptr(), lengths.data_ptr(), offsets.data_ptr(),
+                   b.nstreams, outb.data_ptr(), sh())
+
+    ms_b = _time_graph(torch, run_batch, 10, stream)
+    rate_b = b.total / (ms_b / 1e3)
+    out["batched_ragged"] = {
+        "streams": b.nstreams, "samples": b.total, "ms": ms_b, "Gsamples_per_s": rate_b / 1e9,
+        "GBps": rate_b * 4 / 1e9, "per_sample_vs_plain": rate_b / plain_rate,
+        "launch": [C.sq_variant_name(2, cfgb.variant), cfgb.block, cfgb.ctas_per_sm],
+        "timing": "CUDA graph of one persistent launch, 10 replays"}
+    del outb, keys, bases, lengths, offsets
+    torch.cuda.empty_cache()
+
+    # transforms, 2^30 outputs each
+    key = int(sq.make_keys(11, 1)[0])
+    n = 1 << 30
+    buf = torch.empty(n * 4, dtype=torch.uint8, device=dev)
+    for name, kid, fn, es in (("uniform_f32", C.SQ_KERNEL_UNIFORM_F32, C.sq_uniform_f32, 4),
+                              ("uniform_bf16", C.SQ_KERNEL_UNIFORM_BF16, C.sq_uniform_bf16, 2),
+                              ("normal_f32", C.SQ_KERNEL_NORMAL_F32, C.sq_normal_f32, 4)):
+        C.sq_autotune(kid, n)
+        ms = _time_launches(torch, lambda: fn(key, 0, n, buf.data_ptr(), sh()), 10, stream)
+        out[name] = {"Gsamples_per_s": n / (ms / 1e3) / 1e9, "GBps": n * es / (ms / 1e3) / 1e9,
+                     "ms": ms}
+    del buf
+    torch.cuda.empty_cache()
+
+    # generation-only statistics, 2^20 streams x 2^18 counters
+    S, cps = 1 << 20, 1 << 18
+    fk = torch.from_numpy(sq.make_keys(13, S).view(np.int64)).to(dev)
+    fb = torch.zeros(S, dtype=torch.int64, device=dev)
+    fx = torch.empty(S, dtype=torch.int32, device=dev)
+    fs = torch.empty(S, dtype=torch.int64, device=dev)
+    fh = torch.empty(256, dtype=torch.int64, device=dev)
+    ms = _time_launches(torch, lambda: C.sq_fused_stats(fk.data_ptr(), fb.data_ptr(), S, cps,
+                                                        fx.data_ptr(), fs.data_ptr(),
+                                                        fh.data_ptr(), sh()), 3, stream)
+    props = torch.cuda.get_device_properties(dev)
+    peaks, _ = measured_peaks()
+    int_peak = props.multi_processor_count * IMAD_LANES_PER_SM_CLK * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    rate = S * cps / (ms / 1e3)
+    out["fused_stats"] = {"Gsamples_per_s": rate / 1e9, "ms": ms,
+                          "frac_int": rate / (int_peak / IMAD_SLOTS_SQ32)}
+
+    # context: cuRAND Philox4x32-10 (library call) on the same GPU
+    out["curand_philox4x32_10"] = curand_context(torch, dev, stream)
+    return out
+
+
+def curand_context(torch, dev, stream):
+    import ctypes
+
+    n = 1 << 32
+    for name in ("libcurand.so", "libcurand.so.10", "/usr/local/cuda/lib64/libcurand.so"):
+        try:
+            lib = ctypes.CDLL(name)
+            break
+        except OSError:
+            lib = None
+    if lib is None:
+        return {"unavailable": "libcurand not found"}
+    gen = ctypes.c_void_p()
+    CURAND_RNG_PSEUDO_PHILOX4_32_10 = 161
+    if lib.curandCreateGenerator(ctypes.byref(gen), CURAND_RNG_PSEUDO_PHILOX4_32_10) != 0:
+        return {"unavailable": "curandCreateGenerator failed"}
+    try:
+        lib.curandSetStream(gen, ctypes.c_void_p(int(stream.cuda_stream)))
+        buf = torch.empty(n, dtype=torch.int32, device=dev)
+        fn = lambda: lib.curandGenerate(gen, ctypes.c_void_p(buf.data_ptr()), ctypes.c_size_t(n))  # noqa: E731
+        ms = _time_launches(torch, fn, 5, stream)
+        del buf
+        return {"Gsamples_per_s": n / (ms / 1e3) / 1e9, "ms": ms, "n": n,
+                "call": "curandGenerate (uint32), CURAND_RNG_PSEUDO_PHILOX4_32_10, 2^32 outputs"}
+    finally:
+        lib.curandDestroyGenerator(gen)
+        torch.cuda.empty_cache()
+
+
+def profile_case(args):
+    """A small case of one kernel for ncu: 2 warm-up launches and 3 measured
+    ones on --profile-n outputs (default 2^28: 1 GiB of uint32, larger than
+    L2), default launch table unless --no-tune is absent."""
+    import numpy as np
+    import torch
+
+    import paper_2004_06278_gb300 as sq
+    from paper_2004_06278_gb300 import _lib as C
+    from paper_2004_06278_gb300 import workloads
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    sh = int(torch.cuda.current_stream().cuda_stream)
+    n = args.profile_n
+    key = int(sq.make_keys(2, 1)[0])
+    base = workloads.throughput_base(3)
+    kids = {"u32": C.SQ_KERNEL_U32, "u64": C.SQ_KERNEL_U64, "batch": C.SQ_KERNEL_BATCH,
+            "uniform_f32": C.SQ_KERNEL_UNIFORM_F32, "uniform_bf16": C.SQ_KERNEL_UNIFORM_BF16,
+            "normal_f32": C.SQ_KERNEL_NORMAL_F32, "fused": C.SQ_KERNEL_FUSED}
+    if not args.no_tune:
+        C.sq_autotune(kids[args.profile], n)
+    if args.profile == "fused":
+        S, cps = max(1, n >> 18), 1 << 18
+        k = torch.from_numpy(sq.make_keys(13, S).view(np.int64)).to(dev)
+        b = torch.zeros(S, dtype=torch.int64, device=dev)
+        x = torch.empty(S, dtype=torch.int32, device=dev)
+        s_ = torch.empty(S, dtype=torch.int64, device=dev)
+        h = torch.empty(256, dtype=torch.int64, device=dev)
+        run = lambda: C.sq_fused_stats(k.data_ptr(), b.data_ptr(), S, cps, x.data_ptr(),  # noqa: E731
+                                       s_.data_ptr(), h.data_ptr(), sh)
+    elif args.profile == "batch":
+        bt = workloads.ragged_batch(64, seed=7, lo=n / 128, hi=n / 48)
+        k = torch.from_numpy(sq.make_keys(7, bt.nstreams).view(np.int64)).to(dev)
+        bb = torch.from_numpy(bt.bases.view(np.int64)).to(dev)
+        ll = torch.from_numpy(bt.lengths).to(dev)
+        oo = torch.from_numpy(bt.offsets).to(dev)
+        out = torch.empty(bt.total, dtype=torch.int32, device=dev)
+        run = lambda: C.sq_batch(k.data_ptr(), bb.data_ptr(), ll.data_ptr(), oo.data_ptr(),  # noqa: E731
+                                 bt.nstreams, out.data_ptr(), sh)
+    else:
+        fn = {"u32": C.sq_u32, "u64": C.sq_u64, "uniform_f32": C.sq_uniform_f32,
+              "uniform_bf16": C.sq_uniform_bf16, "normal_f32": C.sq_normal_f32}[args.profile]
+        es = {"u64": 8, "uniform_bf16": 2}.get(args.profile, 4)
+        out = torch.empty(n * es, dtype=torch.uint8, device=dev)
+        run = lambda: fn(key, base, n, out.data_ptr(), sh)  # noqa: E731
+    for _ in range(5):
+        run()
+    torch.cuda.synchronize()
+    print(f"profile case {args.profile} n={n} done", flush=True)
+    return 0
+
+
+def main():
+    args = parse_args()
+    rank, world, local = dist_env()
+    if args.profile:
+        return profile_case(args)
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+    return run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,51 @@
+// Internal C++ interface between the C ABI (api.cpp) and the kernel
+// translation units. Not installed; the public interface is squares.h.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "squares.h"
+
+namespace sq {
+
+struct Cfg {
+    int variant;
+    int block;
+    int ctas_per_sm;  // 0 = as many as fit
+};
+
+// Streaming multiprocessors of the current device (cached per device).
+int current_sm_count();
+
+// --- plain generators (sq_u32, sq_u64, uniform, bf16, normal) -------------
+// kernel_id is one of SQ_KERNEL_U32, _U64, _UNIFORM_F32, _UNIFORM_BF16,
+// _NORMAL_F32. `out` is the caller's buffer; element type per kernel.
+int plain_num_variants();
+const char *plain_variant_name(int variant);
+cudaError_t launch_plain(int kernel_id, const Cfg &cfg, uint64_t key, uint64_t ctr_base,
+                         size_t n, void *out, cudaStream_t stream);
+int plain_max_ctas_per_sm(int kernel_id, int variant, int block);
+
+// --- ragged batch --------------------------------------------------------
+int batch_num_variants();
+const char *batch_variant_name(int variant);
+cudaError_t launch_batch(const Cfg &cfg, const uint64_t *keys, const uint64_t *bases,
+                         const int64_t *lengths, const int64_t *offsets, size_t nstreams,
+                         uint32_t *out, cudaStream_t stream);
+int batch_max_ctas_per_sm(int variant, int block);
+
+// --- generation-only statistics -----------------------------------------
+int fused_num_variants();
+const char *fused_variant_name(int variant);
+cudaError_t launch_fused(const Cfg &cfg, const uint64_t *keys, const uint64_t *bases,
+                         size_t nstreams, uint64_t ctrs_per_stream, uint32_t *xor_out,
+                         uint64_t *sum_top, uint64_t *hist256, cudaStream_t stream);
+int fused_max_ctas_per_sm(int variant, int block);
+
+// --- keys (host) ---------------------------------------------------------
+int make_keys(uint64_t seed, size_t n, uint64_t *keys);
+
+}  // namespace sq

@@ -1,0 +1,134 @@
+// Generation-only statistics: squares32 values are consumed in registers.
+//
+// Work is split into items (stream s, part p); one warp takes an item and
+// each lane walks a contiguous run of its counters by Weyl addition. A lane
+// keeps its XOR and top-byte sum in registers; the warp combines them with
+// shuffles and lane 0 merges them into the stream's outputs with one atomic
+// each (the outputs were cleared on the stream beforehand, so the result
+// does not depend on how streams are split into parts). The top-byte
+// histogram is kept per warp in shared memory and flushed to the global
+// 256-bin histogram at the end, or earlier if a warp's 32-bit bins could
+// overflow. Nothing but the statistics is written to global memory.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "squares_core.cuh"
+
+namespace sq {
+namespace {
+
+constexpr uint64_t kFlushEvery = 1ull << 31;  // counters per warp between flushes
+
+__device__ __forceinline__ void flush_hist(uint32_t *h, uint64_t *__restrict__ hist, int lane) {
+    __syncwarp();
+    for (int b = lane; b < 256; b += 32) {
+        const uint32_t v = h[b];
+        if (v) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(hist + b), static_cast<unsigned long long>(v));
+            h[b] = 0;
+        }
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(512)
+    fused_kernel(const uint64_t *__restrict__ keys, const uint64_t *__restrict__ bases, uint64_t S,
+                 uint64_t C, uint64_t parts, uint64_t part_len, uint32_t *__restrict__ xor_out,
+                 uint64_t *__restrict__ sum_top, uint64_t *__restrict__ hist) {
+    extern __shared__ uint32_t sh_hist[];
+    const int lane = threadIdx.x & 31;
+    uint32_t *h = sh_hist + (threadIdx.x >> 5) * 256;
+    for (int b = lane; b < 256; b += 32) h[b] = 0;
+    __syncwarp();
+
+    const uint64_t gwarp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+    const uint64_t items = S * parts;
+    uint64_t since_flush = 0;
+    for (uint64_t w = gwarp; w < items; w += nwarps) {
+        const uint64_t s = w / parts;
+        const uint64_t a = (w - s * parts) * part_len;
+        const uint64_t b = (a + part_len < C) ? a + part_len : C;
+        const uint64_t per_lane = (b - a + 31) / 32;
+        const uint64_t la = a + lane * per_lane;
+        const uint64_t lb = (la + per_lane < b) ? la + per_lane : b;
+        const uint64_t key = __ldg(keys + s);
+        uint64_t y = (__ldg(bases + s) + la) * key;
+        uint32_t x = 0, sum = 0;
+        const uint64_t cnt = (lb > la) ? lb - la : 0;
+#pragma unroll 4
+        for (uint64_t i = 0; i < cnt; ++i) {
+            const uint64_t yn = y + key;
+            const uint32_t u = squares32_yz(y, yn);
+            y = yn;
+            x ^= u;
+            sum += u >> 24;
+            atomicAdd(h + (u >> 24), 1u);
+        }
+        uint64_t sum64 = sum;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            x ^= __shfl_xor_sync(0xFFFFFFFFu, x, o);
+            sum64 += __shfl_xor_sync(0xFFFFFFFFu, sum64, o);
+        }
+        if (lane == 0) {
+            atomicXor(xor_out + s, x);
+            atomicAdd(reinterpret_cast<unsigned long long *>(sum_top + s),
+                      static_cast<unsigned long long>(sum64));
+        }
+        since_flush += b - a;
+        if (since_flush >= kFlushEvery) {
+            flush_hist(h, hist, lane);
+            since_flush = 0;
+        }
+    }
+    flush_hist(h, hist, lane);
+}
+
+}  // namespace
+
+int fused_num_variants() { return 1; }
+
+const char *fused_variant_name(int variant) { return variant == 0 ? "warp-item" : nullptr; }
+
+int fused_max_ctas_per_sm(int variant, int block) {
+    (void)variant;
+    int blocks = 0;
+    const size_t smem = static_cast<size_t>(block / 32) * 256 * sizeof(uint32_t);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fused_kernel, block, smem) != cudaSuccess)
+        return 1;
+    return blocks > 0 ? blocks : 1;
+}
+
+cudaError_t launch_fused(const Cfg &cfg, const uint64_t *keys, const uint64_t *bases,
+                         size_t nstreams, uint64_t ctrs_per_stream, uint32_t *xor_out,
+                         uint64_t *sum_top, uint64_t *hist256, cudaStream_t stream) {
+    cudaError_t err = cudaMemsetAsync(hist256, 0, 256 * sizeof(uint64_t), stream);
+    if (err != cudaSuccess) return err;
+    if (nstreams == 0) return cudaSuccess;
+    err = cudaMemsetAsync(xor_out, 0, nstreams * sizeof(uint32_t), stream);
+    if (err != cudaSuccess) return err;
+    err = cudaMemsetAsync(sum_top, 0, nstreams * sizeof(uint64_t), stream);
+    if (err != cudaSuccess) return err;
+    if (ctrs_per_stream == 0) return cudaSuccess;
+
+    const int ctas = cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : fused_max_ctas_per_sm(0, cfg.block);
+    const uint64_t grid = static_cast<uint64_t>(current_sm_count()) * ctas;
+    const uint64_t warps = grid * (cfg.block / 32);
+    // Parts per stream: each item at most 2^29 counters (so a lane's 32-bit
+    // top-byte sum cannot overflow), and at least ~4 items per warp when
+    // there are few streams, but never parts shorter than 1024 counters.
+    uint64_t parts = (ctrs_per_stream + (1ull << 29) - 1) >> 29;
+    const uint64_t want = (4 * warps + nstreams - 1) / nstreams;
+    const uint64_t max_parts = (ctrs_per_stream + 1023) / 1024;
+    if (want > parts) parts = want < max_parts ? want : max_parts;
+    if (parts == 0) parts = 1;
+    const uint64_t part_len = (ctrs_per_stream + parts - 1) / parts;
+    parts = (ctrs_per_stream + part_len - 1) / part_len;
+    const size_t smem = static_cast<size_t>(cfg.block / 32) * 256 * sizeof(uint32_t);
+    fused_kernel<<<static_cast<unsigned>(grid), cfg.block, smem, stream>>>(
+        keys, bases, nstreams, ctrs_per_stream, parts, part_len, xor_out, sum_top, hist256);
+    return cudaGetLastError();
+}
+
+}  // namespace sq

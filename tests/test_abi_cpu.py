@@ -1,0 +1,134 @@
+"""The C-ABI library without a GPU: it loads, exports every symbol that
+include/squares.h declares, makes the same keys as the oracle, and rejects
+bad arguments on the host before touching CUDA. No kernel is launched."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2004_06278_gb300 as sq
+from paper_2004_06278_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "squares.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2004_06278_gb300 import build
+
+    build.build()
+    return sq.load()
+
+
+def header_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sq_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = header_functions()
+    assert len(declared) >= 20
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(_lib.declared_symbols()) == declared
+
+
+def test_abi_version(lib):
+    assert sq.sq_abi_version() == 100
+
+
+def test_make_keys_matches_oracle(lib):
+    for seed, n in [(1, 1), (7, 4096), (13, 1 << 16), (0, 5), ((1 << 64) - 1, 100)]:
+        assert np.array_equal(sq.make_keys(seed, n), oracle.make_keys(seed, n)), (seed, n)
+
+
+def test_make_keys_errors(lib):
+    sq.sq_make_keys(1, 0, 0)  # n = 0 is fine, even with NULL
+    with pytest.raises(sq.SquaresError) as e:
+        sq.sq_make_keys(1, 5, 0)
+    assert e.value.status == sq.SQ_EINVAL
+    with pytest.raises(sq.SquaresError) as e:
+        sq.sq_make_keys(1, (1 << 31) + 1, 0)
+    assert e.value.status == sq.SQ_ERANGE
+
+
+@pytest.mark.parametrize("fn,elem", [(sq.sq_u32, 4), (sq.sq_u64, 8), (sq.sq_uniform_f32, 4),
+                                     (sq.sq_uniform_bf16, 2), (sq.sq_normal_f32, 4)])
+def test_plain_argument_checks(lib, fn, elem):
+    fn(1, 0, 0, 0)  # n = 0: no launch, OK
+    with pytest.raises(sq.SquaresError) as e:
+        fn(1, 0, 10, 0)
+    assert e.value.status == sq.SQ_EINVAL and "NULL" in e.value.message
+    if elem > 1:
+        with pytest.raises(sq.SquaresError) as e:
+            fn(1, 0, 10, 0x1000 + 1)
+        assert e.value.status == sq.SQ_EINVAL and "aligned" in e.value.message
+    with pytest.raises(sq.SquaresError) as e:
+        fn(1, 0, (1 << 62) + 1, 0x1000)
+    assert e.value.status == sq.SQ_ERANGE
+
+
+def test_batch_and_fused_argument_checks(lib):
+    sq.sq_batch(0, 0, 0, 0, 0, 0)  # empty batch
+    with pytest.raises(sq.SquaresError) as e:
+        sq.sq_batch(0, 0x1000, 0x1000, 0x1000, 3, 0x1000)
+    assert e.value.status == sq.SQ_EINVAL
+    with pytest.raises(sq.SquaresError) as e:
+        sq.sq_batch(0x1000, 0x1000, 0x1004, 0x1000, 3, 0x1000)
+    assert e.value.status == sq.SQ_EINVAL and "misaligned" in e.value.message
+    with pytest.raises(sq.SquaresError) as e:
+        sq.sq_batch(0x1000, 0x1000, 0x1000, 0x1000, (1 << 31) + 1, 0x1000)
+    assert e.value.status == sq.SQ_ERANGE
+    with pytest.raises(sq.SquaresError) as e:
+        sq.sq_fused_stats(0x1000, 0x1000, 4, 16, 0x1000, 0x1000, 0)
+    assert e.value.status == sq.SQ_EINVAL
+    with pytest.raises(sq.SquaresError) as e:
+        sq.sq_fused_stats(0x1000, 0x1000, 4, (1 << 40) + 1, 0x1000, 0x1000, 0x1000)
+    assert e.value.status == sq.SQ_ERANGE
+    with pytest.raises(sq.SquaresError):
+        sq.sq_graph_launch(0)
+    sq.sq_graph_destroy(0)
+
+
+def test_config_table(lib):
+    assert sq.sq_num_variants(sq.SQ_KERNEL_U32) == 4
+    assert sq.sq_variant_name(sq.SQ_KERNEL_U32, 0) == "st32"
+    assert sq.sq_variant_name(sq.SQ_KERNEL_U32, 99) is None
+    cfg = sq.sq_get_config(sq.SQ_KERNEL_U64, 1 << 20)
+    assert (cfg.variant, cfg.block) == (0, 256)
+    sq.sq_set_config(sq.SQ_KERNEL_U64, 1 << 20, 1, 512, 2)
+    got = sq.sq_get_config(sq.SQ_KERNEL_U64, (1 << 20) + 5)  # same size bucket
+    assert (got.variant, got.block, got.ctas_per_sm) == (1, 512, 2)
+    other = sq.sq_get_config(sq.SQ_KERNEL_U64, 1 << 10)
+    assert (other.variant, other.block) == (0, 256)
+    sq.sq_set_config(sq.SQ_KERNEL_U64, 0, 0, 256, 0)  # all buckets back
+    with pytest.raises(sq.SquaresError):
+        sq.sq_set_config(sq.SQ_KERNEL_U64, 0, 9, 256, 0)
+    with pytest.raises(sq.SquaresError):
+        sq.sq_set_config(sq.SQ_KERNEL_U64, 0, 0, 100, 0)
+    with pytest.raises(sq.SquaresError):
+        sq.sq_get_config(42, 0)
+    with pytest.raises(sq.SquaresError):
+        sq.sq_num_variants(-1)
+
+
+def test_autotune_file_errors(lib, tmp_path):
+    with pytest.raises(sq.SquaresError):
+        sq.sq_autotune_load(str(tmp_path / "missing.txt"))
+    bad = tmp_path / "bad.txt"
+    bad.write_text("not a tune file\n")
+    with pytest.raises(sq.SquaresError):
+        sq.sq_autotune_load(str(bad))
+
+
+def test_last_error_is_per_call(lib):
+    with pytest.raises(sq.SquaresError):
+        sq.sq_u32(1, 0, 10, 0)
+    assert "NULL" in sq.sq_last_error()
+    sq.sq_u32(1, 0, 0, 0)
+    assert sq.sq_last_error() == ""

@@ -1,0 +1,156 @@
+"""GPU parity of the ragged batch (sq_batch) against the oracle: gaps and
+empty streams, wrapping bases, key-counter mode (Section 4), every launch
+variant, CUDA-graph capture and replay, and the debug validator."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2004_06278_gb300 import _lib as C
+from paper_2004_06278_gb300 import workloads
+from tests.gpu_util import CANARY, Guarded, filled_u32, host_u32, stream_handle, to_dev
+
+pytestmark = pytest.mark.gpu
+FILL = np.uint32(CANARY * 0x01010101)
+
+
+def _device_inputs(gpu_lib, b):
+    import torch
+
+    keys = to_dev(gpu_lib.make_keys(b.key_seed, b.nstreams))
+    return keys, to_dev(b.bases), to_dev(b.lengths), to_dev(b.offsets)
+
+
+def _expect(b, n_out):
+    out = np.full(n_out, FILL, dtype=np.uint32)
+    oracle.batch32(oracle.make_keys(b.key_seed, b.nstreams), b.bases, b.lengths, b.offsets, out)
+    return out
+
+
+def _run(gpu_lib, b, offset_elems=0, extra=37):
+    keys, bases, lengths, offsets = _device_inputs(gpu_lib, b)
+    n_out = b.total + extra
+    g = Guarded(4 * n_out, 4 * offset_elems)
+    C.sq_batch(keys.data_ptr(), bases.data_ptr(), lengths.data_ptr(), offsets.data_ptr(),
+               b.nstreams, g.ptr, stream_handle())
+    assert g.guards_intact()
+    return g.payload(np.uint32), n_out
+
+
+@pytest.mark.parametrize("seed,S,max_len", [(1, 1, 10), (2, 5, 3), (3, 37, 3000),
+                                            (4, 300, 20_000), (5, 64, 70_000), (6, 2000, 50)])
+def test_small_batches(gpu_lib, seed, S, max_len):
+    b = workloads.small_ragged_batch(S, seed=seed, max_len=max_len)
+    for off in (0, 1, 3, 5):
+        got, n_out = _run(gpu_lib, b, off)
+        assert np.array_equal(got, _expect(b, n_out)), off
+
+
+def test_leading_gap_and_empty_streams(gpu_lib):
+    b = workloads.small_ragged_batch(50, seed=11, max_len=5000, gap_max=700)
+    b.offsets = b.offsets + 12345  # nothing before offsets[0] is written
+    b.lengths[[0, 7, 8, 49]] = 0
+    got, n_out = _run(gpu_lib, b)
+    assert np.array_equal(got, _expect(b, n_out))
+    assert np.all(got[:12345] == FILL)
+
+
+def test_key_counter_mode(gpu_lib):
+    """Section 4: counter fixed at 0, one output per key."""
+    b = workloads.key_counter_batch(1 << 16, seed=17)
+    got, n_out = _run(gpu_lib, b)
+    assert np.array_equal(got, _expect(b, n_out))
+
+
+def test_every_launch_config(gpu_lib):
+    b = workloads.small_ragged_batch(200, seed=21, max_len=40_000)
+    try:
+        for v in range(C.sq_num_variants(C.SQ_KERNEL_BATCH)):
+            for block in (128, 256, 512):
+                for ctas in (1, 3, 0):
+                    C.sq_set_config(C.SQ_KERNEL_BATCH, 0, v, block, ctas)
+                    got, n_out = _run(gpu_lib, b, offset_elems=block % 7)
+                    assert np.array_equal(got, _expect(b, n_out)), (v, block, ctas)
+    finally:
+        C.sq_set_config(C.SQ_KERNEL_BATCH, 0, 0, 256, 0)
+
+
+def test_batch_equals_plain_per_stream(gpu_lib):
+    import torch
+
+    b = workloads.ragged_batch(64, seed=23, lo=1e3, hi=3e5)
+    got, _ = _run(gpu_lib, b)
+    keys = gpu_lib.make_keys(b.key_seed, b.nstreams)
+    for s in range(b.nstreams):
+        n = int(b.lengths[s])
+        plain = gpu_lib.u32(int(keys[s]), int(b.bases[s]), n).cpu().numpy()
+        a = int(b.offsets[s])
+        assert np.array_equal(got[a:a + n], plain), s
+    torch.cuda.synchronize()
+
+
+def test_torch_graph_capture_and_replay(gpu_lib):
+    """The launch is capture-safe: capture once, change lengths/offsets/bases
+    on the device, replay, and get the new batch."""
+    import torch
+
+    b1 = workloads.small_ragged_batch(100, seed=31, max_len=10_000)
+    b2 = workloads.small_ragged_batch(100, seed=32, max_len=10_000)
+    b2.key_seed = b1.key_seed
+    n_out = max(b1.total, b2.total) + 11
+    keys, bases, lengths, offsets = _device_inputs(gpu_lib, b1)
+    out = filled_u32(n_out, int(FILL))
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        gpu_lib.batch(keys, bases, lengths, offsets, out)  # warm-up outside capture
+        s.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            gpu_lib.batch(keys, bases, lengths, offsets, out)
+    out.copy_(filled_u32(n_out, int(FILL)))
+    g.replay()
+    assert np.array_equal(host_u32(out), _expect(b1, n_out))
+    bases.copy_(to_dev(b2.bases))
+    lengths.copy_(to_dev(b2.lengths))
+    offsets.copy_(to_dev(b2.offsets))
+    out.copy_(filled_u32(n_out, int(FILL)))
+    for _ in range(3):
+        g.replay()
+    assert np.array_equal(host_u32(out), _expect(b2, n_out))
+
+
+def test_native_graph_helper(gpu_lib):
+    import torch
+
+    b = workloads.small_ragged_batch(80, seed=41, max_len=20_000)
+    keys, bases, lengths, offsets = _device_inputs(gpu_lib, b)
+    n_out = b.total + 3
+    out = filled_u32(n_out, int(FILL))
+    torch.cuda.synchronize()
+    graph = C.sq_batch_graph_create(keys.data_ptr(), bases.data_ptr(), lengths.data_ptr(),
+                                    offsets.data_ptr(), b.nstreams, out.data_ptr())
+    try:
+        for _ in range(4):
+            C.sq_graph_launch(graph, stream_handle())
+        assert np.array_equal(host_u32(out), _expect(b, n_out))
+    finally:
+        C.sq_graph_destroy(graph)
+
+
+def test_validate(gpu_lib):
+    import torch
+
+    b = workloads.small_ragged_batch(20, seed=51, max_len=100)
+    _, _, lengths, offsets = _device_inputs(gpu_lib, b)
+    C.sq_batch_validate(lengths.data_ptr(), offsets.data_ptr(), b.nstreams, stream_handle())
+    bad = b.offsets.copy()
+    bad[5] = bad[4] + b.lengths[4] - 1 if b.lengths[4] > 0 else bad[4] - 1
+    offsets.copy_(to_dev(bad))
+    with pytest.raises(C.SquaresError) as e:
+        C.sq_batch_validate(lengths.data_ptr(), offsets.data_ptr(), b.nstreams, stream_handle())
+    assert e.value.status == C.SQ_EINVAL
+    neg = b.lengths.copy()
+    neg[3] = -1
+    lengths.copy_(to_dev(neg))
+    offsets.copy_(to_dev(b.offsets))
+    with pytest.raises(C.SquaresError):
+        C.sq_batch_validate(lengths.data_ptr(), offsets.data_ptr(), b.nstreams, stream_handle())

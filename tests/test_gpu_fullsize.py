@@ -1,0 +1,146 @@
+"""Full-size parity: every output of the benchmark workloads, generated in the
+launch configuration the benchmark uses, compared with the oracle chunk by
+chunk on the host (the oracle runs on all host cores).
+
+  squares64, 2^30 outputs, and squares32, 2^32 outputs, one key (seed 2),
+  counter base uniform in [0, 2^64);
+  squares32, 2^24 outputs from counter 0, key of seed 1;
+  the ragged batch of 4096 streams (seed 7, wrapping streams);
+  uniform FP32 / BF16 (exact) and normals (error bounds), 2^30 each;
+  generation-only statistics, 2^20 streams x 2^18 counters.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2004_06278_gb300 import _lib as C
+from paper_2004_06278_gb300 import workloads
+from tests.gpu_util import stream_handle, to_dev
+from tests.test_gpu_transforms import ABS_TOL, REL_TOL, normal_errors
+
+pytestmark = pytest.mark.gpu
+
+CHUNK = 1 << 27  # elements compared per step
+
+
+def _compare_chunks(dev_tensor, n, expect_fn, np_dtype):
+    import torch
+
+    torch.cuda.synchronize()
+    for a in range(0, n, CHUNK):
+        b = min(n, a + CHUNK)
+        got = dev_tensor[a:b].cpu().numpy().view(np_dtype)
+        want = expect_fn(a, b - a)
+        if not np.array_equal(got, want):
+            bad = np.nonzero(got != want)[0]
+            raise AssertionError(f"mismatch at {a + int(bad[0])}: {got[bad[0]]} != {want[bad[0]]}"
+                                 f" ({bad.size} in chunk)")
+
+
+def test_u64_2p30_all_outputs(gpu_lib):
+    import torch
+
+    key = int(gpu_lib.make_keys(2, 1)[0])
+    base = workloads.throughput_base(3)
+    n = 1 << 30
+    out = torch.empty(n, dtype=torch.int64, device="cuda")
+    C.sq_u64(key, base, n, out.data_ptr(), stream_handle())
+    _compare_chunks(out, n, lambda a, m: oracle.fill64(key, (base + a) % (1 << 64), m), np.uint64)
+    del out
+    torch.cuda.empty_cache()
+
+
+def test_u32_2p32_all_outputs(gpu_lib):
+    import torch
+
+    key = int(gpu_lib.make_keys(2, 1)[0])
+    base = workloads.throughput_base(3)
+    n = 1 << 32
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    C.sq_u32(key, base, n, out.data_ptr(), stream_handle())
+    _compare_chunks(out, n, lambda a, m: oracle.fill32(key, (base + a) % (1 << 64), m), np.uint32)
+    del out
+    torch.cuda.empty_cache()
+
+
+def test_batched_4096_all_outputs(gpu_lib):
+    import torch
+
+    b = workloads.ragged_batch(4096, seed=7)
+    assert b.total > 4_000_000_000
+    wrapping = [s for s in range(b.nstreams)
+                if int(b.bases[s]) + int(b.lengths[s]) > (1 << 64)]
+    assert len(wrapping) == 64
+    keys_dev = gpu_lib.make_keys(b.key_seed, b.nstreams)
+    keys_or = oracle.make_keys(b.key_seed, b.nstreams)
+    out = torch.empty(b.total, dtype=torch.int32, device="cuda")
+    C.sq_batch(to_dev(keys_dev).data_ptr(), to_dev(b.bases).data_ptr(), to_dev(b.lengths).data_ptr(),
+               to_dev(b.offsets).data_ptr(), b.nstreams, out.data_ptr(), stream_handle())
+
+    def expect(a, m):
+        res = np.empty(m, dtype=np.uint32)
+        s0 = int(np.searchsorted(b.offsets, a, side="right") - 1)
+        s = s0
+        while s < b.nstreams and int(b.offsets[s]) < a + m:
+            lo = max(a, int(b.offsets[s]))
+            hi = min(a + m, int(b.offsets[s] + b.lengths[s]))
+            if hi > lo:
+                res[lo - a:hi - a] = oracle.fill32(int(keys_or[s]),
+                                                   (int(b.bases[s]) + lo - int(b.offsets[s])) % (1 << 64),
+                                                   hi - lo)
+            s += 1
+        return res
+
+    _compare_chunks(out, b.total, expect, np.uint32)
+    del out
+    torch.cuda.empty_cache()
+
+
+def test_transforms_2p30(gpu_lib):
+    import torch
+
+    key = int(gpu_lib.make_keys(11, 1)[0])
+    n = 1 << 30
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    C.sq_uniform_f32(key, 0, n, out.data_ptr(), stream_handle())
+    _compare_chunks(out, n, lambda a, m: oracle.uniform_f32(key, a, m).view(np.uint32), np.uint32)
+    C.sq_normal_f32(key, 0, n, out.data_ptr(), stream_handle())
+    torch.cuda.synchronize()
+    worst_abs, worst_rel, tails = 0.0, 0.0, 0
+    for a in range(0, n, CHUNK):
+        m = min(CHUNK, n - a)
+        got = out[a:a + m].cpu().numpy().view(np.float32)
+        want = oracle.normal_f64(key, a // 2, m)
+        ea, er, nt = normal_errors(got, want)
+        worst_abs, worst_rel, tails = max(worst_abs, ea), max(worst_rel, er), tails + nt
+    assert worst_abs <= ABS_TOL and worst_rel <= REL_TOL, (worst_abs, worst_rel)
+    assert tails > 1000
+    del out
+    out16 = torch.empty(n, dtype=torch.int16, device="cuda")
+    C.sq_uniform_bf16(key, 0, n, out16.data_ptr(), stream_handle())
+    _compare_chunks(out16, n, lambda a, m: oracle.uniform_bf16(key, a, m), np.uint16)
+    del out16
+    torch.cuda.empty_cache()
+
+
+def test_fused_2p20_streams_2p18_counters(gpu_lib):
+    import torch
+
+    S, cps = 1 << 20, 1 << 18
+    keys_dev = gpu_lib.make_keys(13, S)
+    keys_or = oracle.make_keys(13, S)
+    bases = np.zeros(S, dtype=np.uint64)
+    xor = torch.empty(S, dtype=torch.int32, device="cuda")
+    sums = torch.empty(S, dtype=torch.int64, device="cuda")
+    hist = torch.empty(256, dtype=torch.int64, device="cuda")
+    C.sq_fused_stats(to_dev(keys_dev).data_ptr(), to_dev(bases).data_ptr(), S, cps, xor.data_ptr(),
+                     sums.data_ptr(), hist.data_ptr(), stream_handle())
+    torch.cuda.synchronize()
+    x = xor.cpu().numpy().view(np.uint32)
+    s = sums.cpu().numpy().view(np.uint64)
+    h = hist.cpu().numpy().view(np.uint64)
+    ex, es, eh = oracle.fused_stats(keys_or, bases, cps)
+    assert np.array_equal(x, ex)
+    assert np.array_equal(s, es)
+    assert np.array_equal(h, eh)
+    assert int(h.sum()) == S * cps

@@ -1,0 +1,122 @@
+"""GPU parity of the plain generators through the C ABI: sq_u32 (Section 2),
+sq_u64 (Section 5), bit for bit against the oracle, at ragged sizes, every
+alignment offset, wrapping counter bases, odd and degenerate keys, and every
+launch variant."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2004_06278_gb300 import _lib as C
+from tests.gpu_util import Guarded, stream_handle
+
+pytestmark = pytest.mark.gpu
+
+M64 = (1 << 64) - 1
+SIZES = [1, 2, 3, 4, 5, 7, 8, 9, 15, 16, 17, 31, 33, 127, 1000, 4097, 65537, (1 << 20) + 3]
+
+
+def _run(fn, elem, key, base, n, offset_elems=0):
+    g = Guarded(n * elem, offset_elems * elem)
+    fn(key, base, n, g.ptr, stream_handle())
+    assert g.guards_intact(), "write outside [out, out + n)"
+    return g.payload({4: np.uint32, 8: np.uint64}[elem])
+
+
+def test_single_stream_2p24_seed1(gpu_lib):
+    """2^24 counters from 0 with the first key of seed 1, all outputs."""
+    key = int(gpu_lib.make_keys(1, 1)[0])
+    n = 1 << 24
+    got = _run(C.sq_u32, 4, key, 0, n)
+    assert np.array_equal(got, oracle.fill32(key, 0, n))
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_u32_sizes_and_offsets(gpu_lib, n):
+    key = int(gpu_lib.make_keys(3, 1)[0])
+    base = 0x123456789ABCDEF0
+    want = oracle.fill32(key, base, n)
+    for off in range(8):
+        assert np.array_equal(_run(C.sq_u32, 4, key, base, n, off), want), (n, off)
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_u64_sizes_and_offsets(gpu_lib, n):
+    key = int(gpu_lib.make_keys(4, 1)[0])
+    base = 0xFEDCBA9876543210
+    want = oracle.fill64(key, base, n)
+    for off in range(4):
+        assert np.array_equal(_run(C.sq_u64, 8, key, base, n, off), want), (n, off)
+
+
+def test_wraparound(gpu_lib):
+    """Counters wrap modulo 2^64 (C semantics of the paper's uint64_t)."""
+    key = int(gpu_lib.make_keys(5, 1)[0])
+    for base in (M64, M64 - 6, (1 << 64) - 100_000):
+        n = 300_001
+        assert np.array_equal(_run(C.sq_u32, 4, key, base, n), oracle.fill32(key, base, n))
+        assert np.array_equal(_run(C.sq_u64, 8, key, base, n), oracle.fill64(key, base, n))
+
+
+@pytest.mark.parametrize("key", [0, 1, 2, M64, 1 << 63, 0x8000000000000001, 0x5555555555555555,
+                                 0xAAAAAAAAAAAAAAAA])
+def test_degenerate_keys(gpu_lib, key):
+    n = 40_000
+    base = 0x0123456789ABCDEF
+    assert np.array_equal(_run(C.sq_u32, 4, key, base, n), oracle.fill32(key, base, n))
+    assert np.array_equal(_run(C.sq_u64, 8, key, base, n), oracle.fill64(key, base, n))
+
+
+def test_random_keys_and_bases(gpu_lib):
+    rng = np.random.default_rng(99)
+    for _ in range(12):
+        key = int(rng.integers(0, 1 << 64, dtype=np.uint64))
+        base = int(rng.integers(0, 1 << 64, dtype=np.uint64))
+        n = int(rng.integers(1, 200_000))
+        assert np.array_equal(_run(C.sq_u32, 4, key, base, n), oracle.fill32(key, base, n))
+        assert np.array_equal(_run(C.sq_u64, 8, key, base, n), oracle.fill64(key, base, n))
+
+
+def test_split_invariance(gpu_lib):
+    """gen(base, n) == gen(base, m) ++ gen(base + m, n - m): the state is
+    (key, ctr), so resuming at ctr + m continues the stream."""
+    key = int(gpu_lib.make_keys(6, 1)[0])
+    base = M64 - 12345
+    n = 1_000_003
+    whole = _run(C.sq_u32, 4, key, base, n)
+    for m in (1, 3, 4097, 500_001):
+        a = _run(C.sq_u32, 4, key, base, m)
+        b = _run(C.sq_u32, 4, key, (base + m) & M64, n - m)
+        assert np.array_equal(np.concatenate([a, b]), whole), m
+
+
+@pytest.mark.parametrize("kid,fn,elem", [(C.SQ_KERNEL_U32, C.sq_u32, 4),
+                                         (C.SQ_KERNEL_U64, C.sq_u64, 8)])
+def test_every_launch_config(gpu_lib, kid, fn, elem):
+    """Each body variant, block size and grid size gives identical bits."""
+    key = int(gpu_lib.make_keys(8, 1)[0])
+    base = M64 - 77
+    n = 3 * 152 * 512 * 8 + 13
+    want = oracle.fill32(key, base, n) if elem == 4 else oracle.fill64(key, base, n)
+    try:
+        for v in range(C.sq_num_variants(kid)):
+            for block in (128, 256, 512):
+                for ctas in (1, 2, 0):
+                    C.sq_set_config(kid, 0, v, block, ctas)
+                    for off in (0, 1):
+                        assert np.array_equal(_run(fn, elem, key, base, n, off), want), (v, block, ctas)
+    finally:
+        C.sq_set_config(kid, 0, 0, 256, 0)
+
+
+def test_async_on_torch_stream(gpu_lib):
+    """Launches go to the caller's stream."""
+    import torch
+
+    key = int(gpu_lib.make_keys(9, 1)[0])
+    s = torch.cuda.Stream()
+    n = 1 << 22
+    out = torch.empty(n, dtype=torch.uint32, device="cuda")
+    with torch.cuda.stream(s):
+        gpu_lib.u32(key, 5, n, out=out)
+    s.synchronize()
+    assert np.array_equal(out.cpu().numpy(), oracle.fill32(key, 5, n))

@@ -1,0 +1,111 @@
+"""GPU parity of the distribution transforms against the oracle: uniform FP32
+and BF16 bit for bit; normals within 2e-6 absolute where |z| < 5 and 1e-5
+relative beyond, against the FP64 Box-Muller values of the same integers."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2004_06278_gb300 import _lib as C
+from tests.gpu_util import Guarded, stream_handle
+
+pytestmark = pytest.mark.gpu
+
+ABS_TOL = 2e-6   # |z| < 5
+REL_TOL = 1e-5   # |z| >= 5
+
+
+def _run(fn, elem, dtype, key, base, n, off=0):
+    g = Guarded(n * elem, off * elem)
+    fn(key, base, n, g.ptr, stream_handle())
+    assert g.guards_intact()
+    return g.payload(dtype)
+
+
+def normal_errors(z32: np.ndarray, z64: np.ndarray):
+    z = z32.astype(np.float64)
+    err = np.abs(z - z64)
+    core = np.abs(z64) < 5
+    max_abs = float(err[core].max()) if core.any() else 0.0
+    tail = ~core
+    max_rel = float((err[tail] / np.abs(z64[tail])).max()) if tail.any() else 0.0
+    return max_abs, max_rel, int(tail.sum())
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 8, 9, 17, 1000, 65537, (1 << 22) + 5])
+def test_uniform_f32_exact(gpu_lib, n):
+    key = int(gpu_lib.make_keys(11, 1)[0])
+    want = oracle.uniform_f32(key, 0, n)
+    for off in (0, 1, 3):
+        got = _run(C.sq_uniform_f32, 4, np.float32, key, 0, n, off)
+        assert np.array_equal(got.view(np.uint32), want.view(np.uint32)), (n, off)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 15, 16, 17, 33, 1001, (1 << 22) + 7])
+def test_uniform_bf16_exact(gpu_lib, n):
+    key = int(gpu_lib.make_keys(11, 1)[0])
+    base = (1 << 64) - 333
+    want = oracle.uniform_bf16(key, base, n)
+    for off in (0, 1, 2, 5, 15):
+        got = _run(C.sq_uniform_bf16, 2, np.uint16, key, base, n, off)
+        assert np.array_equal(got, want), (n, off)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 8, 9, 1001, 65536, (1 << 22) + 3])
+def test_normal_within_bounds(gpu_lib, n):
+    key = int(gpu_lib.make_keys(11, 1)[0])
+    want = oracle.normal_f64(key, 5, n)
+    for off in (0, 1, 2):  # off = 1 leaves pairs unaligned to 8 bytes
+        got = _run(C.sq_normal_f32, 4, np.float32, key, 5, n, off)
+        max_abs, max_rel, _ = normal_errors(got, want)
+        assert max_abs <= ABS_TOL and max_rel <= REL_TOL, (n, off, max_abs, max_rel)
+
+
+def test_normal_edge_integers(gpu_lib):
+    """Counters whose squares64 outputs have hi near 0 (deep tail), near
+    2^31 (the switch to log1p) and near 2^32 - 1 (u1 -> 1, r -> 0): found by
+    scanning the oracle's outputs, then generated on the GPU."""
+    key = int(gpu_lib.make_keys(11, 1)[0])
+    n_pairs = 1 << 24
+    v = oracle.fill64(key, 0, n_pairs)
+    hi = v >> np.uint64(32)
+    picks = np.concatenate([np.argsort(hi)[:64], np.argsort(hi)[-64:],
+                            np.argsort(np.abs(hi.astype(np.int64) - (1 << 31)))[:64]])
+    for j in picks:
+        j = int(j)
+        got = _run(C.sq_normal_f32, 4, np.float32, key, j, 2)
+        want = oracle.normal_f64(key, j, 2)
+        max_abs, max_rel, _ = normal_errors(got, want)
+        assert max_abs <= ABS_TOL and max_rel <= REL_TOL, (j, hex(int(v[j])), got, want)
+
+
+def test_normal_large_sample_error_report(gpu_lib):
+    """2^26 normals: the stated bounds hold and the tail is populated."""
+    key = int(gpu_lib.make_keys(11, 1)[0])
+    n = 1 << 26
+    got = _run(C.sq_normal_f32, 4, np.float32, key, 0, n)
+    want = oracle.normal_f64(key, 0, n)
+    max_abs, max_rel, ntail = normal_errors(got, want)
+    assert max_abs <= ABS_TOL and max_rel <= REL_TOL, (max_abs, max_rel)
+    assert ntail > 0
+
+
+def test_transform_variants(gpu_lib):
+    key = int(gpu_lib.make_keys(12, 1)[0])
+    n = 2 * 152 * 512 * 16 + 5
+    wf = oracle.uniform_f32(key, 3, n).view(np.uint32)
+    wb = oracle.uniform_bf16(key, 3, n)
+    wn = oracle.normal_f64(key, 3, n)
+    try:
+        for v in range(4):
+            for block in (128, 512):
+                for kid in (C.SQ_KERNEL_UNIFORM_F32, C.SQ_KERNEL_UNIFORM_BF16, C.SQ_KERNEL_NORMAL_F32):
+                    C.sq_set_config(kid, 0, v, block, 0)
+                got = _run(C.sq_uniform_f32, 4, np.float32, key, 3, n, 1)
+                assert np.array_equal(got.view(np.uint32), wf), (v, block)
+                assert np.array_equal(_run(C.sq_uniform_bf16, 2, np.uint16, key, 3, n, 3), wb)
+                z = _run(C.sq_normal_f32, 4, np.float32, key, 3, n, 2)
+                max_abs, max_rel, _ = normal_errors(z, wn)
+                assert max_abs <= ABS_TOL and max_rel <= REL_TOL
+    finally:
+        for kid in (C.SQ_KERNEL_UNIFORM_F32, C.SQ_KERNEL_UNIFORM_BF16, C.SQ_KERNEL_NORMAL_F32):
+            C.sq_set_config(kid, 0, 0, 256, 0)
