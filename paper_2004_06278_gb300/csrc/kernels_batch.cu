@@ -107,12 +107,12 @@ __global__ void __launch_bounds__(512)
                 uint64_t ys[EPV + 1];
                 ys[0] = y;
 #pragma unroll
-                for (int j = 0; j < EPV; ++j) ys[j + 1] = ys[j] + key;
+                for (int j = 0; j < EPV; ++j) ys[j + 1] = add64(ys[j], key);
                 uint32_t w[EPV];
 #pragma unroll
                 for (int j = 0; j < EPV; ++j) w[j] = squares32_yz(ys[j], ys[j + 1]);
                 store32B<CS>(p, w);
-                y += ystep;
+                y = add64(y, ystep);
                 p += tile;
             }
             t += k;

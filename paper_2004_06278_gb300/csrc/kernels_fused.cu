@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(512)
         const uint64_t cnt = (lb > la) ? lb - la : 0;
 #pragma unroll 4
         for (uint64_t i = 0; i < cnt; ++i) {
-            const uint64_t yn = y + key;
+            const uint64_t yn = add64(y, key);
             const uint32_t u = squares32_yz(y, yn);
             y = yn;
             x ^= u;

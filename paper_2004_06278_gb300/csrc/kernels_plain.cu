@@ -29,7 +29,7 @@ struct OpU32 {
         uint64_t ys[W + 1];
         ys[0] = y;
 #pragma unroll
-        for (int j = 0; j < W; ++j) ys[j + 1] = ys[j] + key;
+        for (int j = 0; j < W; ++j) ys[j + 1] = add64(ys[j], key);
 #pragma unroll
         for (int j = 0; j < W; ++j) w[j] = squares32_yz(ys[j], ys[j + 1]);
     }
@@ -47,7 +47,7 @@ struct OpU64 {
         uint64_t ys[C + 1];
         ys[0] = y;
 #pragma unroll
-        for (int j = 0; j < C; ++j) ys[j + 1] = ys[j] + key;
+        for (int j = 0; j < C; ++j) ys[j + 1] = add64(ys[j], key);
 #pragma unroll
         for (int j = 0; j < C; ++j) {
             const uint64_t v = squares64_yz(ys[j], ys[j + 1]);
@@ -68,7 +68,7 @@ struct OpUniformF32 {
         uint64_t ys[W + 1];
         ys[0] = y;
 #pragma unroll
-        for (int j = 0; j < W; ++j) ys[j + 1] = ys[j] + key;
+        for (int j = 0; j < W; ++j) ys[j + 1] = add64(ys[j], key);
 #pragma unroll
         for (int j = 0; j < W; ++j) w[j] = __float_as_uint(uniform24(squares32_yz(ys[j], ys[j + 1])));
     }
@@ -86,7 +86,7 @@ struct OpUniformBF16 {
         uint64_t ys[C + 1];
         ys[0] = y;
 #pragma unroll
-        for (int j = 0; j < C; ++j) ys[j + 1] = ys[j] + key;
+        for (int j = 0; j < C; ++j) ys[j + 1] = add64(ys[j], key);
 #pragma unroll
         for (int j = 0; j < W; ++j) {
             const float a = uniform24(squares32_yz(ys[2 * j], ys[2 * j + 1]));
@@ -108,7 +108,7 @@ struct OpNormalF32 {
         uint64_t ys[C + 1];
         ys[0] = y;
 #pragma unroll
-        for (int j = 0; j < C; ++j) ys[j + 1] = ys[j] + key;
+        for (int j = 0; j < C; ++j) ys[j + 1] = add64(ys[j], key);
 #pragma unroll
         for (int j = 0; j < C; ++j) {
             const uint64_t v = squares64_yz(ys[j], ys[j + 1]);
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(512)
         uint32_t w[W];
         Op::template chunk<W>(y, key, w);
         store_chunk<BYTES, CS>(p, w);
-        y += ystep;
+        y = add64(y, ystep);
         p += pstep;
     }
 }

@@ -74,8 +74,11 @@ def test_batched_4096_all_outputs(gpu_lib):
     keys_dev = gpu_lib.make_keys(b.key_seed, b.nstreams)
     keys_or = oracle.make_keys(b.key_seed, b.nstreams)
     out = torch.empty(b.total, dtype=torch.int32, device="cuda")
-    C.sq_batch(to_dev(keys_dev).data_ptr(), to_dev(b.bases).data_ptr(), to_dev(b.lengths).data_ptr(),
-               to_dev(b.offsets).data_ptr(), b.nstreams, out.data_ptr(), stream_handle())
+    # keep the device inputs referenced until the kernel has run
+    d_keys, d_bases = to_dev(keys_dev), to_dev(b.bases)
+    d_lengths, d_offsets = to_dev(b.lengths), to_dev(b.offsets)
+    C.sq_batch(d_keys.data_ptr(), d_bases.data_ptr(), d_lengths.data_ptr(), d_offsets.data_ptr(),
+               b.nstreams, out.data_ptr(), stream_handle())
 
     def expect(a, m):
         res = np.empty(m, dtype=np.uint32)
@@ -114,7 +117,7 @@ def test_transforms_2p30(gpu_lib):
         ea, er, nt = normal_errors(got, want)
         worst_abs, worst_rel, tails = max(worst_abs, ea), max(worst_rel, er), tails + nt
     assert worst_abs <= ABS_TOL and worst_rel <= REL_TOL, (worst_abs, worst_rel)
-    assert tails > 1000
+    assert tails > 300  # P(|z| >= 5) * 2^30 is about 615
     del out
     out16 = torch.empty(n, dtype=torch.int16, device="cuda")
     C.sq_uniform_bf16(key, 0, n, out16.data_ptr(), stream_handle())
@@ -133,7 +136,8 @@ def test_fused_2p20_streams_2p18_counters(gpu_lib):
     xor = torch.empty(S, dtype=torch.int32, device="cuda")
     sums = torch.empty(S, dtype=torch.int64, device="cuda")
     hist = torch.empty(256, dtype=torch.int64, device="cuda")
-    C.sq_fused_stats(to_dev(keys_dev).data_ptr(), to_dev(bases).data_ptr(), S, cps, xor.data_ptr(),
+    d_keys, d_bases = to_dev(keys_dev), to_dev(bases)
+    C.sq_fused_stats(d_keys.data_ptr(), d_bases.data_ptr(), S, cps, xor.data_ptr(),
                      sums.data_ptr(), hist.data_ptr(), stream_handle())
     torch.cuda.synchronize()
     x = xor.cpu().numpy().view(np.uint32)
