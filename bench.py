@@ -60,8 +60,10 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-tune", action="store_true", help="use the default launch table")
     p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--tune-file", help="load the launch table from this file if it exists "
+                                       "(no tuning); otherwise tune and save it there")
     p.add_argument("--profile", choices=["u32", "u64", "batch", "uniform_f32", "uniform_bf16",
-                                         "normal_f32", "fused"],
+                                         "normal_f32", "uniform2_f32", "uniform_f64", "fused"],
                    help="run one kernel on a small case (for ncu) instead of the benchmark")
     p.add_argument("--profile-n", type=int, default=1 << 28)
     return p.parse_args()
@@ -233,7 +235,7 @@ def source_hash(*rel):
 
 
 KERNEL_SOURCES = ("paper_2004_06278_gb300/csrc/kernels_plain.cu",
-                  "paper_2004_06278_gb300/csrc/squares_core.cuh")
+                  "paper_2004_06278_gb300/csrc/stores.cuh", "include/squares_device.cuh")
 
 
 def profiled_traffic(name: str):
@@ -296,7 +298,10 @@ def run_ours(args, rank, world, local):
     base32 = shard_base(base0, N32, rank)
     out64 = torch.empty(N64, dtype=torch.int64, device=dev)
     out32 = torch.empty(N32, dtype=torch.int32, device=dev)
-    if not args.no_tune:
+    tuned_from_file = bool(args.tune_file and os.path.exists(args.tune_file))
+    if tuned_from_file:
+        C.sq_autotune_load(args.tune_file)
+    elif not args.no_tune:
         C.sq_autotune(C.SQ_KERNEL_U64, N64)
         C.sq_autotune(C.SQ_KERNEL_U32, N32)
     cfg32 = C.sq_get_config(C.SQ_KERNEL_U32, N32)
@@ -387,7 +392,7 @@ def run_ours(args, rank, world, local):
                                              cfg32.ctas_per_sm],
                                   "sq_u64": [C.sq_variant_name(1, cfg64.variant), cfg64.block,
                                              cfg64.ctas_per_sm],
-                                  "tuned": not args.no_tune}},
+                                  "tuned": "file" if tuned_from_file else not args.no_tune}},
             "roofline": roof,
             "clocks": clock_info,
             "gpu_launches": 2 * args.steps,
@@ -398,7 +403,9 @@ def run_ours(args, rank, world, local):
     if rank == 0 and not args.no_e2e:
         result["e2e"] = e2e_block(torch, C, key, base64, base32, dev, args.e2e_steps)
     if rank == 0 and not args.no_extras:
-        result["breakdown"] = breakdown(torch, sq, C, workloads, dev, ms32)
+        result["breakdown"] = breakdown(torch, sq, C, workloads, dev, ms32, tuned_from_file)
+    if rank == 0 and args.tune_file and not tuned_from_file:
+        C.sq_autotune_save(args.tune_file)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline_block()
     if rank == 0:
@@ -508,7 +515,7 @@ def _time_launches(torch, fn, reps, stream):
     return a.elapsed_time(b) / reps
 
 
-def breakdown(torch, sq, C, workloads, dev, ms32_plain):
+def breakdown(torch, sq, C, workloads, dev, ms32_plain, tuned_from_file=False):
     import numpy as np
 
     out = {}
@@ -525,7 +532,9 @@ def breakdown(torch, sq, C, workloads, dev, ms32_plain):
     offsets = torch.from_numpy(b.offsets).to(dev)
     outb = torch.empty(b.total, dtype=torch.int32, device=dev)
     torch.cuda.synchronize()  # inputs were copied on the default stream
-    C.sq_autotune(C.SQ_KERNEL_BATCH, b.total)
+    if not tuned_from_file:
+        C.sq_autotune_batch(keys.data_ptr(), bases.data_ptr(), lengths.data_ptr(),
+                            offsets.data_ptr(), b.nstreams, outb.data_ptr())
     cfgb = C.sq_get_config(C.SQ_KERNEL_BATCH, 0)
 
     def run_batch():
@@ -549,7 +558,8 @@ def breakdown(torch, sq, C, workloads, dev, ms32_plain):
     for name, kid, fn, es in (("uniform_f32", C.SQ_KERNEL_UNIFORM_F32, C.sq_uniform_f32, 4),
                               ("uniform_bf16", C.SQ_KERNEL_UNIFORM_BF16, C.sq_uniform_bf16, 2),
                               ("normal_f32", C.SQ_KERNEL_NORMAL_F32, C.sq_normal_f32, 4)):
-        C.sq_autotune(kid, n)
+        if not tuned_from_file:
+            C.sq_autotune(kid, n)
         ms = _time_launches(torch, lambda: fn(key, 0, n, buf.data_ptr(), sh()), 10, stream)
         out[name] = {"Gsamples_per_s": n / (ms / 1e3) / 1e9, "GBps": n * es / (ms / 1e3) / 1e9,
                      "ms": ms}
@@ -626,10 +636,20 @@ def profile_case(args):
     key = int(sq.make_keys(2, 1)[0])
     base = workloads.throughput_base(3)
     kids = {"u32": C.SQ_KERNEL_U32, "u64": C.SQ_KERNEL_U64, "batch": C.SQ_KERNEL_BATCH,
+            "uniform2_f32": C.SQ_KERNEL_UNIFORM2_F32, "uniform_f64": C.SQ_KERNEL_UNIFORM_F64,
             "uniform_f32": C.SQ_KERNEL_UNIFORM_F32, "uniform_bf16": C.SQ_KERNEL_UNIFORM_BF16,
             "normal_f32": C.SQ_KERNEL_NORMAL_F32, "fused": C.SQ_KERNEL_FUSED}
-    if not args.no_tune:
+    if args.tune_file and os.path.exists(args.tune_file):
+        # use the configuration tuned for the benchmark's size of this kernel
+        C.sq_autotune_load(args.tune_file)
+        full = {"u32": N32, "u64": N64}.get(args.profile, 1 << 30)
+        c = C.sq_get_config(kids[args.profile], full)
+        C.sq_set_config(kids[args.profile], n, c.variant, c.block, c.ctas_per_sm)
+    elif not args.no_tune:
         C.sq_autotune(kids[args.profile], n)
+    c = C.sq_get_config(kids[args.profile], n)
+    print(f"profile config: {C.sq_variant_name(kids[args.profile], c.variant)} block {c.block} "
+          f"ctas/SM {c.ctas_per_sm}", flush=True)
     if args.profile == "fused":
         S, cps = max(1, n >> 18), 1 << 18
         k = torch.from_numpy(sq.make_keys(13, S).view(np.int64)).to(dev)
@@ -650,8 +670,9 @@ def profile_case(args):
                                  bt.nstreams, out.data_ptr(), sh)
     else:
         fn = {"u32": C.sq_u32, "u64": C.sq_u64, "uniform_f32": C.sq_uniform_f32,
-              "uniform_bf16": C.sq_uniform_bf16, "normal_f32": C.sq_normal_f32}[args.profile]
-        es = {"u64": 8, "uniform_bf16": 2}.get(args.profile, 4)
+              "uniform_bf16": C.sq_uniform_bf16, "normal_f32": C.sq_normal_f32,
+              "uniform2_f32": C.sq_uniform2_f32, "uniform_f64": C.sq_uniform_f64}[args.profile]
+        es = {"u64": 8, "uniform_bf16": 2, "uniform_f64": 8}.get(args.profile, 4)
         out = torch.empty(n * es, dtype=torch.uint8, device=dev)
         run = lambda: fn(key, base, n, out.data_ptr(), sh)  # noqa: E731
     for _ in range(5):

@@ -76,6 +76,29 @@ int sq_u32(uint64_t key, uint64_t ctr_base, size_t n, uint32_t *out, sq_stream_t
 int sq_u64(uint64_t key, uint64_t ctr_base, size_t n, uint64_t *out, sq_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Strided counters (Section 4: counter increments other than one).
+ * sq_u32_strided: out[i] = squares32(ctr_base + i*stride mod 2^64, key).
+ * sq_u64_strided: out[i] = squares64(ctr_base + i*stride mod 2^64, key).
+ * Any stride is valid, including 0 (every element the same). out [device].
+ * Errors as for sq_u32.
+ * ---------------------------------------------------------------------- */
+int sq_u32_strided(uint64_t key, uint64_t ctr_base, uint64_t stride, size_t n, uint32_t *out,
+                   sq_stream_t stream);
+int sq_u64_strided(uint64_t key, uint64_t ctr_base, uint64_t stride, size_t n, uint64_t *out,
+                   sq_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Key-counter mode (Section 4: the counter fixed, the key varying).
+ * sq_keys_u32: out[i] = squares32(ctr, keys[i]);  sq_keys_u64: squares64.
+ * keys [device, uint64_t[nkeys]], out [device]. SQ_EINVAL for NULL or
+ * misaligned arrays with nkeys > 0; SQ_ERANGE if nkeys > 2^62.
+ * ---------------------------------------------------------------------- */
+int sq_keys_u32(const uint64_t *keys, size_t nkeys, uint64_t ctr, uint32_t *out,
+                sq_stream_t stream);
+int sq_keys_u64(const uint64_t *keys, size_t nkeys, uint64_t ctr, uint64_t *out,
+                sq_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Ragged batch of squares32 streams in one persistent launch (Section 3:
  * many keys, each with its own 2^64 counter space).
  * For every stream s < nstreams and i < lengths[s]:
@@ -122,6 +145,18 @@ int sq_uniform_bf16(uint64_t key, uint64_t ctr_base, size_t n, uint16_t *out,
                     sq_stream_t stream);
 int sq_normal_f32(uint64_t key, uint64_t ctr_base, size_t n, float *out, sq_stream_t stream);
 
+/* Section 5's 64-bit output used for floating point:
+ * sq_uniform2_f32: two floats per squares64 output v = squares64(ctr_base+j):
+ *                  out[2j] = floor(hi/2^8) 2^-24, out[2j+1] = floor(lo/2^8)
+ *                  2^-24 (hi, lo the upper and lower 32 bits); an odd n drops
+ *                  the last one. Exact.
+ * sq_uniform_f64:  out[i] = floor(squares64(ctr_base+i) / 2^11) 2^-53, a
+ *                  53-bit double in [0, 1), exact; built from integer
+ *                  operations (no FP64 arithmetic on the GPU).
+ * out [device], naturally aligned. Errors as for sq_u32. */
+int sq_uniform2_f32(uint64_t key, uint64_t ctr_base, size_t n, float *out, sq_stream_t stream);
+int sq_uniform_f64(uint64_t key, uint64_t ctr_base, size_t n, double *out, sq_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Generation-only statistics: squares32 values consumed in registers, never
  * stored. For each stream s < nstreams over the counters ctr_bases[s] + i,
@@ -152,7 +187,9 @@ int sq_fused_stats(const uint64_t *keys, const uint64_t *ctr_bases, size_t nstre
 #define SQ_KERNEL_UNIFORM_BF16 4
 #define SQ_KERNEL_NORMAL_F32 5
 #define SQ_KERNEL_FUSED 6
-#define SQ_NUM_KERNELS 7
+#define SQ_KERNEL_UNIFORM2_F32 7
+#define SQ_KERNEL_UNIFORM_F64 8
+#define SQ_NUM_KERNELS 9
 
 typedef struct {
     int32_t variant;     /* kernel body: store width / cache policy, see sq_variant_name */
@@ -174,8 +211,16 @@ int sq_set_config(int kernel_id, size_t n, const sq_launch_config *cfg);
 /* Time every candidate configuration on a problem of size n_hint (in output
  * elements; for SQ_KERNEL_FUSED, total counters) and keep the fastest for
  * that size bucket. Synchronous; allocates and frees a temporary device
- * buffer of at most 1 GiB; must not run during stream capture. */
+ * buffer of at most 2 GiB; must not run during stream capture. */
 int sq_autotune(int kernel_id, size_t n_hint);
+
+/* Tune the ragged-batch kernel on the caller's own batch: every candidate
+ * configuration is launched on these device arrays (each launch writes the
+ * same, correct outputs into out) and the fastest becomes the one sq_batch
+ * uses. Synchronous; allocates no device memory; must not run during stream
+ * capture. Arguments and errors as for sq_batch. */
+int sq_autotune_batch(const uint64_t *keys, const uint64_t *ctr_bases, const int64_t *lengths,
+                      const int64_t *offsets, size_t nstreams, uint32_t *out);
 
 /* Persist / restore the tuned table as a small text file keyed by the
  * device name. Loading entries for another device name is a no-op. */

@@ -12,7 +12,9 @@ Every function names the paper passage it follows:
   squares32 / fill32 / pairs32 ... Section 2 (four-round generator)
   squares64 / fill64 / pairs64 ... Section 5 (five-round, 64-bit output)
   batch32 ........................ ragged batch of Section 2 streams
+  fill32_strided / fill64_strided  strided counters (Section 4)
   uniform_f32 / uniform_bf16 ..... float conversion (Section 5 prose), FP64
+  uniform2_f32 / uniform_f64 ..... two floats / one 53-bit double per squares64
   normal_f64 ..................... Box-Muller on squares64 halves, FP64
   fused_stats .................... XOR / top-byte sum / top-byte histogram
   make_keys ...................... "different digits" keys (Section 3)
@@ -69,6 +71,10 @@ def _load():
             "oracle_hist_w": (None, [_u64, _u, _u, _i, _p]),
             "oracle_fill32": (None, [_u64, _u64, _u64, _p]),
             "oracle_fill64": (None, [_u64, _u64, _u64, _p]),
+            "oracle_fill32_strided": (None, [_u64, _u64, _u64, _u64, _p]),
+            "oracle_fill64_strided": (None, [_u64, _u64, _u64, _u64, _p]),
+            "oracle_uniform2_f32": (None, [_u64, _u64, _u64, _p]),
+            "oracle_uniform_f64": (None, [_u64, _u64, _u64, _p]),
             "oracle_pairs32": (None, [_p, _p, _u64, _p]),
             "oracle_pairs64": (None, [_p, _p, _u64, _p]),
             "oracle_batch32": (None, [_p, _p, _p, _p, _u64, _p]),
@@ -170,6 +176,20 @@ def fill64(key: int, base: int, n: int, threads: int | None = None) -> np.ndarra
     return out
 
 
+def fill32_strided(key: int, base: int, stride: int, n: int) -> np.ndarray:
+    """out[i] = squares32(base + i*stride mod 2^64, key) (Section 4)."""
+    out = np.empty(n, dtype=np.uint32)
+    _load().oracle_fill32_strided(key, base & M64, stride & M64, n, out.ctypes.data)
+    return out
+
+
+def fill64_strided(key: int, base: int, stride: int, n: int) -> np.ndarray:
+    """out[i] = squares64(base + i*stride mod 2^64, key) (Section 4)."""
+    out = np.empty(n, dtype=np.uint64)
+    _load().oracle_fill64_strided(key, base & M64, stride & M64, n, out.ctypes.data)
+    return out
+
+
 def pairs32(ctrs: np.ndarray, keys: np.ndarray) -> np.ndarray:
     """out[i] = squares32(ctrs[i], keys[i])."""
     ctrs = np.ascontiguousarray(ctrs, dtype=np.uint64)
@@ -221,6 +241,20 @@ def uniform_bf16(key: int, base: int, n: int, threads: int | None = None) -> np.
     addr = out.ctypes.data
     _parallel(lambda a, b: lib.oracle_uniform_bf16(key, (base + a) & M64, b - a, addr + 2 * a),
               _chunks(n, threads), threads)
+    return out
+
+
+def uniform2_f32(key: int, base: int, n: int) -> np.ndarray:
+    """Two float uniforms per squares64 output: upper half, then lower."""
+    out = np.empty(n, dtype=np.float32)
+    _load().oracle_uniform2_f32(key, base & M64, n, out.ctypes.data)
+    return out
+
+
+def uniform_f64(key: int, base: int, n: int) -> np.ndarray:
+    """53-bit double uniforms floor(squares64 / 2^11) / 2^53."""
+    out = np.empty(n, dtype=np.float64)
+    _load().oracle_uniform_f64(key, base & M64, n, out.ctypes.data)
     return out
 
 

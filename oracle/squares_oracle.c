@@ -129,7 +129,22 @@ void oracle_fill64(uint64_t key, uint64_t base, uint64_t n, uint64_t *out) {
     for (i = 0; i < n; ++i) out[i] = oracle_squares64(base + i, key);
 }
 
-/* Per-element (counter, key) pairs, for sampled checks. */
+/* Strided counters (Section 4's "increments other than one"):
+ * out[i] = squares32(base + i*stride mod 2^64, key). */
+void oracle_fill32_strided(uint64_t key, uint64_t base, uint64_t stride, uint64_t n,
+                           uint32_t *out) {
+    uint64_t i;
+    for (i = 0; i < n; ++i) out[i] = oracle_squares32(base + i * stride, key);
+}
+
+void oracle_fill64_strided(uint64_t key, uint64_t base, uint64_t stride, uint64_t n,
+                           uint64_t *out) {
+    uint64_t i;
+    for (i = 0; i < n; ++i) out[i] = oracle_squares64(base + i * stride, key);
+}
+
+/* Per-element (counter, key) pairs, for sampled checks and Section 4's
+ * key-counter mode (one counter, many keys). */
 void oracle_pairs32(const uint64_t *ctrs, const uint64_t *keys, uint64_t n,
                     uint32_t *out) {
     uint64_t i;
@@ -189,6 +204,29 @@ void oracle_uniform_bf16(uint64_t key, uint64_t base, uint64_t n,
             const int biased = (e - 1) + 127;      /* v in [2^(e-1), 2^e) */
             out[i] = (uint16_t)((biased << 7) | (q - 128));
         }
+    }
+}
+
+/* Two uniforms per squares64 output (Section 5: the 64 bits split into two
+ * 32-bit halves): output j = squares64(base + j, key) supplies
+ * out[2j] = floor(hi / 2^8) / 2^24 and out[2j+1] = floor(lo / 2^8) / 2^24,
+ * hi and lo its upper and lower 32 bits. An odd n drops the last one. */
+void oracle_uniform2_f32(uint64_t key, uint64_t base, uint64_t n, float *out) {
+    uint64_t j;
+    for (j = 0; 2 * j < n; ++j) {
+        const uint64_t v = oracle_squares64(base + j, key);
+        out[2 * j] = (float)((double)((v >> 32) >> 8) / 16777216.0);
+        if (2 * j + 1 < n) out[2 * j + 1] = (float)((double)((v & 0xffffffffu) >> 8) / 16777216.0);
+    }
+}
+
+/* 53-bit double uniforms (Section 5): floor(squares64 / 2^11) / 2^53, exact
+ * in double precision. */
+void oracle_uniform_f64(uint64_t key, uint64_t base, uint64_t n, double *out) {
+    uint64_t i;
+    for (i = 0; i < n; ++i) {
+        const uint64_t v = oracle_squares64(base + i, key);
+        out[i] = (double)(v >> 11) / 9007199254740992.0;
     }
 }
 

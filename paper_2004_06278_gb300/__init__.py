@@ -13,16 +13,18 @@ from __future__ import annotations
 from . import _lib
 from ._lib import (  # noqa: F401  (re-exported C-ABI names)
     SQ_ECUDA, SQ_EINVAL, SQ_ERANGE, SQ_KERNEL_BATCH, SQ_KERNEL_FUSED, SQ_KERNEL_NORMAL_F32,
-    SQ_KERNEL_U32, SQ_KERNEL_U64, SQ_KERNEL_UNIFORM_BF16, SQ_KERNEL_UNIFORM_F32, SQ_NUM_KERNELS,
-    SQ_OK, SquaresError, load, sq_abi_version, sq_autotune, sq_autotune_load, sq_autotune_save,
-    sq_batch, sq_batch_graph_create, sq_batch_validate, sq_fused_stats, sq_get_config,
-    sq_graph_destroy, sq_graph_launch, sq_last_error, sq_make_keys, sq_normal_f32,
-    sq_num_variants, sq_set_config, sq_u32, sq_u64, sq_uniform_bf16, sq_uniform_f32,
-    sq_variant_name)
+    SQ_KERNEL_U32, SQ_KERNEL_U64, SQ_KERNEL_UNIFORM2_F32, SQ_KERNEL_UNIFORM_BF16,
+    SQ_KERNEL_UNIFORM_F32, SQ_KERNEL_UNIFORM_F64, SQ_NUM_KERNELS, SQ_OK, SquaresError, load,
+    sq_abi_version, sq_autotune, sq_autotune_batch, sq_autotune_load, sq_autotune_save, sq_batch,
+    sq_batch_graph_create, sq_batch_validate, sq_fused_stats, sq_get_config, sq_graph_destroy,
+    sq_graph_launch, sq_keys_u32, sq_keys_u64, sq_last_error, sq_make_keys, sq_normal_f32,
+    sq_num_variants, sq_set_config, sq_u32, sq_u32_strided, sq_u64, sq_u64_strided,
+    sq_uniform2_f32, sq_uniform_bf16, sq_uniform_f32, sq_uniform_f64, sq_variant_name)
 
 __all__ = [n for n in dir(_lib) if n.startswith(("sq_", "SQ_"))] + [
     "SquaresError", "load", "make_keys", "u32", "u64", "uniform_f32", "uniform_bf16",
-    "normal_f32", "batch", "fused_stats"]
+    "normal_f32", "uniform2_f32", "uniform_f64", "u32_strided", "keys_u32", "batch",
+    "fused_stats"]
 
 
 def _stream(stream) -> int:
@@ -92,6 +94,42 @@ def normal_f32(key: int, ctr_base: int, n: int, out=None, stream=None, device=No
 
     out = _out(out, n, torch.float32, device)
     sq_normal_f32(key, ctr_base, n, out.data_ptr(), _stream(stream))
+    return out
+
+
+def uniform2_f32(key: int, ctr_base: int, n: int, out=None, stream=None, device=None):
+    """Two float uniforms per squares64 output (upper half, then lower)."""
+    import torch
+
+    out = _out(out, n, torch.float32, device)
+    sq_uniform2_f32(key, ctr_base, n, out.data_ptr(), _stream(stream))
+    return out
+
+
+def uniform_f64(key: int, ctr_base: int, n: int, out=None, stream=None, device=None):
+    """53-bit double uniforms from squares64 (torch.float64)."""
+    import torch
+
+    out = _out(out, n, torch.float64, device)
+    sq_uniform_f64(key, ctr_base, n, out.data_ptr(), _stream(stream))
+    return out
+
+
+def u32_strided(key: int, ctr_base: int, stride: int, n: int, out=None, stream=None, device=None):
+    """squares32 at counters ctr_base + i*stride (torch.uint32)."""
+    import torch
+
+    out = _out(out, n, torch.uint32, device)
+    sq_u32_strided(key, ctr_base, stride, n, out.data_ptr(), _stream(stream))
+    return out
+
+
+def keys_u32(keys, ctr: int, out=None, stream=None):
+    """squares32(ctr, keys[i]) for a CUDA tensor of keys (key-counter mode)."""
+    import torch
+
+    out = _out(out, keys.numel(), torch.uint32, keys.device)
+    sq_keys_u32(keys.data_ptr(), keys.numel(), ctr, out.data_ptr(), _stream(stream))
     return out
 
 

@@ -28,7 +28,9 @@ SQ_KERNEL_UNIFORM_F32 = 3
 SQ_KERNEL_UNIFORM_BF16 = 4
 SQ_KERNEL_NORMAL_F32 = 5
 SQ_KERNEL_FUSED = 6
-SQ_NUM_KERNELS = 7
+SQ_KERNEL_UNIFORM2_F32 = 7
+SQ_KERNEL_UNIFORM_F64 = 8
+SQ_NUM_KERNELS = 9
 
 _STATUS = {SQ_EINVAL: "SQ_EINVAL", SQ_ECUDA: "SQ_ECUDA", SQ_ERANGE: "SQ_ERANGE"}
 
@@ -55,6 +57,12 @@ _SIGNATURES = {
     "sq_make_keys": [_u64, _sz, _p],
     "sq_u32": [_u64, _u64, _sz, _p, _p],
     "sq_u64": [_u64, _u64, _sz, _p, _p],
+    "sq_u32_strided": [_u64, _u64, _u64, _sz, _p, _p],
+    "sq_u64_strided": [_u64, _u64, _u64, _sz, _p, _p],
+    "sq_keys_u32": [_p, _sz, _u64, _p, _p],
+    "sq_keys_u64": [_p, _sz, _u64, _p, _p],
+    "sq_uniform2_f32": [_u64, _u64, _sz, _p, _p],
+    "sq_uniform_f64": [_u64, _u64, _sz, _p, _p],
     "sq_batch": [_p, _p, _p, _p, _sz, _p, _p],
     "sq_batch_validate": [_p, _p, _sz, _p],
     "sq_uniform_f32": [_u64, _u64, _sz, _p, _p],
@@ -65,6 +73,7 @@ _SIGNATURES = {
     "sq_get_config": [_i, _sz, ctypes.POINTER(sq_launch_config)],
     "sq_set_config": [_i, _sz, ctypes.POINTER(sq_launch_config)],
     "sq_autotune": [_i, _sz],
+    "sq_autotune_batch": [_p, _p, _p, _p, _sz, _p],
     "sq_autotune_save": [ctypes.c_char_p],
     "sq_autotune_load": [ctypes.c_char_p],
     "sq_batch_graph_create": [_p, _p, _p, _p, _sz, _p, ctypes.POINTER(_p)],
@@ -138,6 +147,32 @@ def sq_u64(key: int, ctr_base: int, n: int, out_ptr: int, stream: int = 0) -> No
     _call("sq_u64", key, ctr_base, n, out_ptr, stream)
 
 
+def sq_u32_strided(key: int, ctr_base: int, stride: int, n: int, out_ptr: int,
+                   stream: int = 0) -> None:
+    _call("sq_u32_strided", key, ctr_base, stride, n, out_ptr, stream)
+
+
+def sq_u64_strided(key: int, ctr_base: int, stride: int, n: int, out_ptr: int,
+                   stream: int = 0) -> None:
+    _call("sq_u64_strided", key, ctr_base, stride, n, out_ptr, stream)
+
+
+def sq_keys_u32(keys_ptr: int, nkeys: int, ctr: int, out_ptr: int, stream: int = 0) -> None:
+    _call("sq_keys_u32", keys_ptr, nkeys, ctr, out_ptr, stream)
+
+
+def sq_keys_u64(keys_ptr: int, nkeys: int, ctr: int, out_ptr: int, stream: int = 0) -> None:
+    _call("sq_keys_u64", keys_ptr, nkeys, ctr, out_ptr, stream)
+
+
+def sq_uniform2_f32(key: int, ctr_base: int, n: int, out_ptr: int, stream: int = 0) -> None:
+    _call("sq_uniform2_f32", key, ctr_base, n, out_ptr, stream)
+
+
+def sq_uniform_f64(key: int, ctr_base: int, n: int, out_ptr: int, stream: int = 0) -> None:
+    _call("sq_uniform_f64", key, ctr_base, n, out_ptr, stream)
+
+
 def sq_batch(keys_ptr: int, bases_ptr: int, lengths_ptr: int, offsets_ptr: int, nstreams: int,
              out_ptr: int, stream: int = 0) -> None:
     _call("sq_batch", keys_ptr, bases_ptr, lengths_ptr, offsets_ptr, nstreams, out_ptr, stream)
@@ -190,6 +225,11 @@ def sq_set_config(kernel_id: int, n: int, variant: int, block: int, ctas_per_sm:
 
 def sq_autotune(kernel_id: int, n_hint: int) -> None:
     _call("sq_autotune", kernel_id, n_hint)
+
+
+def sq_autotune_batch(keys_ptr: int, bases_ptr: int, lengths_ptr: int, offsets_ptr: int,
+                      nstreams: int, out_ptr: int) -> None:
+    _call("sq_autotune_batch", keys_ptr, bases_ptr, lengths_ptr, offsets_ptr, nstreams, out_ptr)
 
 
 def sq_autotune_save(path: str) -> None:

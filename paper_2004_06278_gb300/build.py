@@ -19,7 +19,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libsquares.so")
 
-SOURCES = ["api.cpp", "keys.cpp", "kernels_plain.cu", "kernels_batch.cu", "kernels_fused.cu"]
+SOURCES = ["api.cpp", "keys.cpp", "kernels_plain.cu", "kernels_batch.cu", "kernels_fused.cu",
+           "kernels_misc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -41,8 +42,8 @@ def _flags(verbose: bool) -> list[str]:
 def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
-    deps = [src, os.path.join(CSRC, "squares_core.cuh"), os.path.join(CSRC, "internal.h"),
-            os.path.join(INCLUDE, "squares.h"), __file__]
+    deps = [src, os.path.join(CSRC, "stores.cuh"), os.path.join(CSRC, "internal.h"),
+            os.path.join(INCLUDE, "squares.h"), os.path.join(INCLUDE, "squares_device.cuh"), __file__]
     t = os.path.getmtime(obj)
     return any(os.path.getmtime(d) > t for d in deps)
 

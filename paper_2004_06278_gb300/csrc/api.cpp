@@ -58,7 +58,8 @@ bool valid_kernel(int kid) { return kid >= 0 && kid < SQ_NUM_KERNELS; }
 
 bool is_plain(int kid) {
     return kid == SQ_KERNEL_U32 || kid == SQ_KERNEL_U64 || kid == SQ_KERNEL_UNIFORM_F32 ||
-           kid == SQ_KERNEL_UNIFORM_BF16 || kid == SQ_KERNEL_NORMAL_F32;
+           kid == SQ_KERNEL_UNIFORM_BF16 || kid == SQ_KERNEL_NORMAL_F32 ||
+           kid == SQ_KERNEL_UNIFORM2_F32 || kid == SQ_KERNEL_UNIFORM_F64;
 }
 
 int num_variants(int kid) {
@@ -190,6 +191,56 @@ int sq_normal_f32(uint64_t key, uint64_t ctr_base, size_t n, float *out, sq_stre
     return plain_entry(SQ_KERNEL_NORMAL_F32, key, ctr_base, n, out, 4, stream, "sq_normal_f32");
 }
 
+int sq_uniform2_f32(uint64_t key, uint64_t ctr_base, size_t n, float *out, sq_stream_t stream) {
+    return plain_entry(SQ_KERNEL_UNIFORM2_F32, key, ctr_base, n, out, 4, stream, "sq_uniform2_f32");
+}
+
+int sq_uniform_f64(uint64_t key, uint64_t ctr_base, size_t n, double *out, sq_stream_t stream) {
+    return plain_entry(SQ_KERNEL_UNIFORM_F64, key, ctr_base, n, out, 8, stream, "sq_uniform_f64");
+}
+
+static int strided_entry(bool wide, uint64_t key, uint64_t base, uint64_t stride, size_t n, void *out,
+                         sq_stream_t stream, const char *name) {
+    const size_t elem = wide ? 8 : 4;
+    if (n == 0) return ok();
+    if (out == nullptr) return fail(SQ_EINVAL, "%s: out is NULL with n = %zu", name, n);
+    if (!aligned(out, elem)) return fail(SQ_EINVAL, "%s: out is not %zu-byte aligned", name, elem);
+    if (n > kMaxElems) return fail(SQ_ERANGE, "%s: n = %zu exceeds 2^62", name, n);
+    const cudaError_t e = sq::launch_strided(wide, key, base, stride, n, out, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, name);
+    return ok();
+}
+
+int sq_u32_strided(uint64_t key, uint64_t ctr_base, uint64_t stride, size_t n, uint32_t *out,
+                   sq_stream_t stream) {
+    return strided_entry(false, key, ctr_base, stride, n, out, stream, "sq_u32_strided");
+}
+
+int sq_u64_strided(uint64_t key, uint64_t ctr_base, uint64_t stride, size_t n, uint64_t *out,
+                   sq_stream_t stream) {
+    return strided_entry(true, key, ctr_base, stride, n, out, stream, "sq_u64_strided");
+}
+
+static int keys_entry(bool wide, const uint64_t *keys, size_t n, uint64_t ctr, void *out,
+                      sq_stream_t stream, const char *name) {
+    const size_t elem = wide ? 8 : 4;
+    if (n == 0) return ok();
+    if (!keys || !out) return fail(SQ_EINVAL, "%s: NULL array with nkeys = %zu", name, n);
+    if (!aligned(keys, 8) || !aligned(out, elem)) return fail(SQ_EINVAL, "%s: misaligned array", name);
+    if (n > kMaxElems) return fail(SQ_ERANGE, "%s: nkeys = %zu exceeds 2^62", name, n);
+    const cudaError_t e = sq::launch_keys(wide, keys, n, ctr, out, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, name);
+    return ok();
+}
+
+int sq_keys_u32(const uint64_t *keys, size_t nkeys, uint64_t ctr, uint32_t *out, sq_stream_t stream) {
+    return keys_entry(false, keys, nkeys, ctr, out, stream, "sq_keys_u32");
+}
+
+int sq_keys_u64(const uint64_t *keys, size_t nkeys, uint64_t ctr, uint64_t *out, sq_stream_t stream) {
+    return keys_entry(true, keys, nkeys, ctr, out, stream, "sq_keys_u64");
+}
+
 int sq_batch(const uint64_t *keys, const uint64_t *ctr_bases, const int64_t *lengths,
              const int64_t *offsets, size_t nstreams, uint32_t *out, sq_stream_t stream) {
     if (nstreams == 0) return ok();
@@ -317,6 +368,7 @@ cudaError_t time_it(cudaStream_t st, int reps, F run, float *ms) {
 size_t elem_size(int kid) {
     switch (kid) {
         case SQ_KERNEL_U64: return 8;
+        case SQ_KERNEL_UNIFORM_F64: return 8;
         case SQ_KERNEL_UNIFORM_BF16: return 2;
         default: return 4;
     }
@@ -337,7 +389,7 @@ int sq_autotune(int kernel_id, size_t n_hint) {
         ~StreamGuard() { cudaStreamDestroy(s); }
     } guard{st};
 
-    const size_t cap_bytes = size_t(1) << 30;
+    const size_t cap_bytes = size_t(1) << 31;
     DevBuf out, aux;
     std::vector<sq::Cfg> cands;
     const int blocks[3] = {128, 256, 512};
@@ -418,7 +470,7 @@ int sq_autotune(int kernel_id, size_t n_hint) {
             return sq::launch_fused(c, keys, bases, S, cps, xors, sums, hist, st);
         };
         float ms = 0.f;
-        e = time_it(st, 5, launch, &ms);
+        e = time_it(st, 10, launch, &ms);
         if (e != cudaSuccess) return cuda_fail(e, "sq_autotune: candidate launch");
         if (ms < best) {
             best = ms;
@@ -426,6 +478,43 @@ int sq_autotune(int kernel_id, size_t n_hint) {
         }
     }
     table().set(kernel_id, n_hint, best_cfg);
+    return ok();
+}
+
+int sq_autotune_batch(const uint64_t *keys, const uint64_t *ctr_bases, const int64_t *lengths,
+                      const int64_t *offsets, size_t nstreams, uint32_t *out) {
+    if (nstreams == 0) return ok();
+    int rc = batch_checks(keys, ctr_bases, lengths, offsets, nstreams, out, "sq_autotune_batch");
+    if (rc != SQ_OK) return rc;
+    cudaError_t e = cudaDeviceSynchronize();  // inputs may come from any stream
+    if (e != cudaSuccess) return cuda_fail(e, "sq_autotune_batch");
+    cudaStream_t st;
+    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "sq_autotune_batch");
+    float best = 1e30f;
+    sq::Cfg best_cfg = table().get(SQ_KERNEL_BATCH, 0);
+    const int blocks[3] = {128, 256, 512};
+    const int ctas_opts[4] = {1, 2, 4, 0};
+    for (int v = 0; v < sq::batch_num_variants() && e == cudaSuccess; ++v)
+        for (int b : blocks) {
+            const int mx = sq::batch_max_ctas_per_sm(v, b);
+            for (int c : ctas_opts) {
+                if (c > mx) continue;
+                const sq::Cfg cfg{v, b, c};
+                float ms = 0.f;
+                e = time_it(st, 5, [&]() {
+                    return sq::launch_batch(cfg, keys, ctr_bases, lengths, offsets, nstreams, out, st);
+                }, &ms);
+                if (e != cudaSuccess) break;
+                if (ms < best) {
+                    best = ms;
+                    best_cfg = cfg;
+                }
+            }
+        }
+    cudaStreamDestroy(st);
+    if (e != cudaSuccess) return cuda_fail(e, "sq_autotune_batch: candidate launch");
+    table().set(SQ_KERNEL_BATCH, 0, best_cfg);
     return ok();
 }
 

@@ -22,7 +22,7 @@ int current_sm_count();
 
 // --- plain generators (sq_u32, sq_u64, uniform, bf16, normal) -------------
 // kernel_id is one of SQ_KERNEL_U32, _U64, _UNIFORM_F32, _UNIFORM_BF16,
-// _NORMAL_F32. `out` is the caller's buffer; element type per kernel.
+// _NORMAL_F32, _UNIFORM2_F32, _UNIFORM_F64. `out` is the caller's buffer; element type per kernel.
 int plain_num_variants();
 const char *plain_variant_name(int variant);
 cudaError_t launch_plain(int kernel_id, const Cfg &cfg, uint64_t key, uint64_t ctr_base,
@@ -44,6 +44,12 @@ cudaError_t launch_fused(const Cfg &cfg, const uint64_t *keys, const uint64_t *b
                          size_t nstreams, uint64_t ctrs_per_stream, uint32_t *xor_out,
                          uint64_t *sum_top, uint64_t *hist256, cudaStream_t stream);
 int fused_max_ctas_per_sm(int variant, int block);
+
+// --- strided counters and key-counter mode -------------------------------
+cudaError_t launch_strided(bool wide, uint64_t key, uint64_t ctr_base, uint64_t stride, size_t n,
+                           void *out, cudaStream_t stream);
+cudaError_t launch_keys(bool wide, const uint64_t *keys, size_t n, uint64_t ctr, void *out,
+                        cudaStream_t stream);
 
 // --- keys (host) ---------------------------------------------------------
 int make_keys(uint64_t seed, size_t n, uint64_t *keys);

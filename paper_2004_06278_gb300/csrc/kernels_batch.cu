@@ -1,32 +1,42 @@
 // Ragged batch of squares32 streams in one persistent launch.
 //
-// The packed output index space is cut into tiles of blockDim * 8 elements
-// (one 32-byte chunk per thread), aligned to the output's 32-byte boundary.
+// The packed output index space is cut into tiles of blockDim * EPV elements
+// (EPV = 8 or 16 consecutive outputs per thread), aligned to the output's
+// 32-byte boundary.
 // CTA c of the persistent grid owns one contiguous run of tiles, so as it
 // walks its run the stream index only grows: one binary search over the
 // offsets at the start, then a forward step whenever a tile crosses into
 // the next stream. A run of whole tiles inside one stream is generated like
-// the plain kernel (Weyl stepping by tile * key, 32-byte vector stores);
-// a tile that touches a stream boundary, a gap or the end of the batch is
-// written element by element, each element finding its stream by binary
-// search. The batch extent offsets[S-1] + lengths[S-1] is read on the
+// the plain kernel (Weyl stepping by tile * key, 32-byte vector stores). In
+// a tile that touches a stream boundary, a gap or the end of the batch each
+// thread finds the stream of its own chunk by a galloping search forward;
+// chunks inside one stream still take the vector path and only chunks that
+// straddle a boundary are written element by element. The batch extent offsets[S-1] + lengths[S-1] is read on the
 // device, so the launch needs no host-side knowledge of the lengths and can
 // be captured in a CUDA graph. There are no spin-waits and no inter-CTA
 // communication.
 #include <cuda_runtime.h>
 
 #include "internal.h"
-#include "squares_core.cuh"
+#include "squares_device.cuh"
+#include "stores.cuh"
 
 namespace sq {
 namespace {
 
 constexpr uint32_t kNoStream = 0xFFFFFFFFu;
 
-// Largest s in [from, S) with offsets[s] <= e, given offsets[from] <= e.
+// Largest s in [from, S) with offsets[s] <= e, given offsets[from] <= e:
+// gallop forward (from+1, from+2, from+4, ...) then bisect, so a stream d
+// positions ahead costs about 2 log2(d) loads -- one or two at a boundary.
 __device__ __forceinline__ uint32_t find_stream(const int64_t *__restrict__ offsets, uint32_t S,
                                                 uint32_t from, int64_t e) {
-    uint32_t lo = from, hi = S;
+    uint32_t lo = from, step = 1;
+    while (step <= S - 1 - lo && __ldg(offsets + lo + step) <= e) {
+        lo += step;
+        step <<= 1;
+    }
+    uint32_t hi = (step <= S - lo) ? lo + step : S;
     while (hi - lo > 1) {
         const uint32_t mid = lo + (hi - lo) / 2;
         if (__ldg(offsets + mid) <= e) lo = mid; else hi = mid;
@@ -34,39 +44,111 @@ __device__ __forceinline__ uint32_t find_stream(const int64_t *__restrict__ offs
     return lo;
 }
 
-// Writes out[e] if some stream covers position e (and e < end).
-__device__ __forceinline__ void batch_single(const uint64_t *__restrict__ keys,
-                                             const uint64_t *__restrict__ bases,
-                                             const int64_t *__restrict__ lengths,
-                                             const int64_t *__restrict__ offsets, uint32_t S,
-                                             uint32_t from, int64_t e, int64_t end,
-                                             uint32_t *__restrict__ out) {
-    if (e >= end) return;
-    if (from == kNoStream) {
-        if (__ldg(offsets) > e) return;
-        from = 0;
+// squares32 of C consecutive counters from y = ctr*key, e = t(ctr+1) - t(ctr)
+// and c2 = 2*key^2: one squaring for round 1, then additions (the
+// recurrence of round1_delta).
+template <int C>
+__device__ __forceinline__ void run32(uint64_t y, uint64_t e, uint64_t key, uint64_t c2, uint32_t (&w)[C]) {
+    uint64_t t = round1_value(y);
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        const uint64_t z = add64(y, key);
+        w[j] = squares32_tyz(t, y, z);
+        y = z;
+        t = add64(t, e);
+        e = add64(e, c2);
     }
-    const uint32_t s = find_stream(offsets, S, from, e);
-    const int64_t off = __ldg(offsets + s);
-    if (e >= off + __ldg(lengths + s)) return;
-    out[e] = squares32(__ldg(bases + s) + static_cast<uint64_t>(e - off), __ldg(keys + s));
 }
 
-template <bool CS>
+// Stream containing or preceding position e, searching forward from `from`
+// (kNoStream: nothing found yet). kNoStream if e precedes the first stream.
+__device__ __forceinline__ uint32_t stream_at(const int64_t *__restrict__ offsets, uint32_t S,
+                                              uint32_t from, int64_t e) {
+    if (from == kNoStream) {
+        if (__ldg(offsets) > e) return kNoStream;
+        from = 0;
+    }
+    return find_stream(offsets, S, from, e);
+}
+
+// Writes the EPV consecutive positions [e0, e0 + EPV) of a tile that touches
+// a stream boundary, a gap or the end of the batch: a chunk that lies inside
+// one stream is generated and stored like a whole tile; otherwise element by
+// element, walking forward across stream boundaries (Weyl steps inside each
+// stream) and skipping positions that no stream covers.
+template <bool CS, int EPV>
+__device__ __forceinline__ void boundary_chunk(const uint64_t *__restrict__ keys,
+                                               const uint64_t *__restrict__ bases,
+                                               const int64_t *__restrict__ lengths,
+                                               const int64_t *__restrict__ offsets, uint32_t S,
+                                               uint32_t from, int64_t e0, int64_t end,
+                                               uint32_t *__restrict__ out) {
+    if (e0 >= end) return;
+    uint32_t s = stream_at(offsets, S, from, e0);
+    if (s == kNoStream) {  // e0 precedes the first stream: start at stream 0
+        s = 0;
+    }
+    int64_t seg_lo = __ldg(offsets + s);
+    int64_t seg_hi = seg_lo + __ldg(lengths + s);
+    if (seg_lo <= e0 && e0 + EPV <= seg_hi) {
+        const uint64_t key = __ldg(keys + s);
+        const uint64_t y = (__ldg(bases + s) + static_cast<uint64_t>(e0 - seg_lo)) * key;
+        uint32_t w[EPV];
+        run32<EPV>(y, round1_delta(y, key), key, (key * key) << 1, w);
+        store32B<CS>(out + e0, *reinterpret_cast<const uint32_t(*)[8]>(&w[0]));
+        if constexpr (EPV == 16)
+            store32B<CS>(out + e0 + 8, *reinterpret_cast<const uint32_t(*)[8]>(&w[8]));
+        return;
+    }
+    uint64_t key = __ldg(keys + s);
+    uint64_t y = 0;
+    bool have_y = false;
+#pragma unroll 1
+    for (int j = 0; j < EPV; ++j) {
+        const int64_t e = e0 + j;
+        if (e >= end) break;
+        if (e >= seg_hi && s + 1 < S) {  // next stream(s); empty ones are skipped
+            s = find_stream(offsets, S, s, e);
+            seg_lo = __ldg(offsets + s);
+            seg_hi = seg_lo + __ldg(lengths + s);
+            key = __ldg(keys + s);
+            have_y = false;
+        }
+        if (e < seg_lo || e >= seg_hi) continue;  // a gap
+        if (!have_y) {
+            y = (__ldg(bases + s) + static_cast<uint64_t>(e - seg_lo)) * key;
+            have_y = true;
+        }
+        const uint64_t z = add64(y, key);
+        out[e] = squares32_yz(y, z);
+        y = z;
+    }
+}
+
+// EPV consecutive outputs per thread per tile: 8 (one 32-byte store) or 16
+// (two adjacent 32-byte stores).
+template <bool CS, int EPV>
 __global__ void __launch_bounds__(512)
     batch_kernel(const uint64_t *__restrict__ keys, const uint64_t *__restrict__ bases,
                  const int64_t *__restrict__ lengths, const int64_t *__restrict__ offsets,
                  uint32_t S, uint32_t *__restrict__ out, uint32_t head) {
-    constexpr int EPV = 8;  // 32-byte chunks of uint32_t
     const int tile = blockDim.x * EPV;  // a power of two
     const int shift = __ffs(tile) - 1;
     if (S == 0) return;
     const int64_t start = __ldg(offsets);
     const int64_t end = __ldg(offsets + S - 1) + __ldg(lengths + S - 1);
 
-    // Elements before the first 32-byte boundary.
-    if (blockIdx.x == 0 && threadIdx.x < head)
-        batch_single(keys, bases, lengths, offsets, S, kNoStream, threadIdx.x, end, out);
+    // Elements before the first 32-byte boundary (fewer than 8), by CTA 0.
+    if (blockIdx.x == 0) {
+        for (int64_t e = threadIdx.x; e < static_cast<int64_t>(head) && e < end; e += blockDim.x) {
+            const uint32_t s = stream_at(offsets, S, kNoStream, e);
+            if (s != kNoStream) {
+                const int64_t off = __ldg(offsets + s);
+                if (e < off + __ldg(lengths + s))
+                    out[e] = squares32(__ldg(bases + s) + static_cast<uint64_t>(e - off), __ldg(keys + s));
+            }
+        }
+    }
     if (end <= static_cast<int64_t>(head)) return;
 
     const int64_t first = start > static_cast<int64_t>(head) ? start : head;
@@ -77,15 +159,10 @@ __global__ void __launch_bounds__(512)
     const int64_t t_stop = (t + per < t_end) ? t + per : t_end;
     if (t >= t_stop) return;
 
-    int64_t lo = head + (t << shift);
-    uint32_t s = (start <= lo) ? find_stream(offsets, S, 0, lo) : kNoStream;
+    uint32_t s = stream_at(offsets, S, kNoStream, head + (t << shift));
     while (t < t_stop) {
-        lo = head + (t << shift);
-        if (s == kNoStream) {
-            if (start <= lo) s = find_stream(offsets, S, 0, lo);
-        } else if (s + 1 < S && __ldg(offsets + s + 1) <= lo) {
-            s = find_stream(offsets, S, s + 1, lo);
-        }
+        const int64_t lo = head + (t << shift);
+        if (s == kNoStream || (s + 1 < S && __ldg(offsets + s + 1) <= lo)) s = stream_at(offsets, S, s, lo);
         int64_t k = 0;
         int64_t seg_lo = 0;
         if (s != kNoStream) {
@@ -101,38 +178,39 @@ __global__ void __launch_bounds__(512)
             const uint64_t key = __ldg(keys + s);
             const int64_t e = lo + threadIdx.x * EPV;
             uint64_t y = (__ldg(bases + s) + static_cast<uint64_t>(e - seg_lo)) * key;
-            const uint64_t ystep = key << shift;
+            const uint64_t c2 = (key * key) << 1;
+            uint64_t er = round1_delta(y, key);
+            const uint64_t ystep = key << shift;  // one tile of counters
+            const uint64_t estep = c2 << shift;
             uint32_t *p = out + e;
             for (int64_t i = 0; i < k; ++i) {
-                uint64_t ys[EPV + 1];
-                ys[0] = y;
-#pragma unroll
-                for (int j = 0; j < EPV; ++j) ys[j + 1] = add64(ys[j], key);
                 uint32_t w[EPV];
-#pragma unroll
-                for (int j = 0; j < EPV; ++j) w[j] = squares32_yz(ys[j], ys[j + 1]);
-                store32B<CS>(p, w);
+                run32<EPV>(y, er, key, c2, w);
+                store32B<CS>(p, *reinterpret_cast<const uint32_t(*)[8]>(&w[0]));
+                if constexpr (EPV == 16)
+                    store32B<CS>(p + 8, *reinterpret_cast<const uint32_t(*)[8]>(&w[8]));
                 y = add64(y, ystep);
+                er = add64(er, estep);
                 p += tile;
             }
             t += k;
         } else {
-            // A tile at a stream boundary, in a gap, or at the end.
-            const int64_t e0 = lo + threadIdx.x * EPV;
-#pragma unroll 1
-            for (int j = 0; j < EPV; ++j)
-                batch_single(keys, bases, lengths, offsets, S, s, e0 + j, end, out);
+            boundary_chunk<CS, EPV>(keys, bases, lengths, offsets, S, s, lo + threadIdx.x * EPV, end, out);
             t += 1;
         }
     }
 }
 
-constexpr int kBatchVariants = 2;
-const char *kBatchVariantNames[kBatchVariants] = {"st32", "st32.cs"};
+constexpr int kBatchVariants = 4;
+const char *kBatchVariantNames[kBatchVariants] = {"st32", "st32.cs", "st32x2", "st32x2.cs"};
 
 const void *batch_fn(int variant) {
-    return variant == 1 ? reinterpret_cast<const void *>(&batch_kernel<true>)
-                        : reinterpret_cast<const void *>(&batch_kernel<false>);
+    switch (variant) {
+        case 0: return reinterpret_cast<const void *>(&batch_kernel<false, 8>);
+        case 1: return reinterpret_cast<const void *>(&batch_kernel<true, 8>);
+        case 2: return reinterpret_cast<const void *>(&batch_kernel<false, 16>);
+        default: return reinterpret_cast<const void *>(&batch_kernel<true, 16>);
+    }
 }
 
 }  // namespace
@@ -160,10 +238,12 @@ cudaError_t launch_batch(const Cfg &cfg, const uint64_t *keys, const uint64_t *b
     const uintptr_t addr = reinterpret_cast<uintptr_t>(out);
     const uint32_t head = static_cast<uint32_t>(((32 - (addr % 32)) % 32) / 4);
     const uint32_t S = static_cast<uint32_t>(nstreams);
-    if (cfg.variant == 1)
-        batch_kernel<true><<<grid, cfg.block, 0, stream>>>(keys, bases, lengths, offsets, S, out, head);
-    else
-        batch_kernel<false><<<grid, cfg.block, 0, stream>>>(keys, bases, lengths, offsets, S, out, head);
+    switch (cfg.variant) {
+        case 0: batch_kernel<false, 8><<<grid, cfg.block, 0, stream>>>(keys, bases, lengths, offsets, S, out, head); break;
+        case 1: batch_kernel<true, 8><<<grid, cfg.block, 0, stream>>>(keys, bases, lengths, offsets, S, out, head); break;
+        case 2: batch_kernel<false, 16><<<grid, cfg.block, 0, stream>>>(keys, bases, lengths, offsets, S, out, head); break;
+        default: batch_kernel<true, 16><<<grid, cfg.block, 0, stream>>>(keys, bases, lengths, offsets, S, out, head); break;
+    }
     return cudaGetLastError();
 }
 

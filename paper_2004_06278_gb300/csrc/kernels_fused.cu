@@ -12,7 +12,8 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
-#include "squares_core.cuh"
+#include "squares_device.cuh"
+#include "stores.cuh"
 
 namespace sq {
 namespace {
@@ -54,13 +55,18 @@ __global__ void __launch_bounds__(512)
         const uint64_t lb = (la + per_lane < b) ? la + per_lane : b;
         const uint64_t key = __ldg(keys + s);
         uint64_t y = (__ldg(bases + s) + la) * key;
+        uint64_t t = round1_value(y);  // round 1 by the recurrence of round1_delta
+        uint64_t er = round1_delta(y, key);
+        const uint64_t c2 = (key * key) << 1;
         uint32_t x = 0, sum = 0;
         const uint64_t cnt = (lb > la) ? lb - la : 0;
 #pragma unroll 4
         for (uint64_t i = 0; i < cnt; ++i) {
             const uint64_t yn = add64(y, key);
-            const uint32_t u = squares32_yz(y, yn);
+            const uint32_t u = squares32_tyz(t, y, yn);
             y = yn;
+            t = add64(t, er);
+            er = add64(er, c2);
             x ^= u;
             sum += u >> 24;
             atomicAdd(h + (u >> 24), 1u);

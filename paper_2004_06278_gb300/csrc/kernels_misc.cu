@@ -1,0 +1,87 @@
+// Strided counters (Section 4's "increments other than one") and
+// key-counter mode (Section 4: one counter, many keys). Neither is on the
+// throughput path; both write one element per thread per step, coalesced
+// (adjacent threads write adjacent elements).
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "squares_device.cuh"
+
+namespace sq {
+namespace {
+
+// out[e] = squares(ctr0 + e*stride, key): y advances by T*stride*key per
+// step, and z = y + key as the definition asks for whatever the stride.
+template <bool WIDE>
+__global__ void __launch_bounds__(256)
+    strided_kernel(uint64_t key, uint64_t ctr0, uint64_t stride, void *__restrict__ out, uint64_t n) {
+    const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const uint64_t nt = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    if (tid >= n) return;
+    uint64_t y = (ctr0 + tid * stride) * key;
+    const uint64_t ystep = nt * stride * key;
+    for (uint64_t e = tid; e < n; e += nt) {
+        const uint64_t z = add64(y, key);
+        if constexpr (WIDE)
+            static_cast<uint64_t *>(out)[e] = squares64_yz(y, z);
+        else
+            static_cast<uint32_t *>(out)[e] = squares32_yz(y, z);
+        y = add64(y, ystep);
+    }
+}
+
+// out[e] = squares(ctr, keys[e]).
+template <bool WIDE>
+__global__ void __launch_bounds__(256)
+    keys_kernel(const uint64_t *__restrict__ keys, uint64_t n, uint64_t ctr, void *__restrict__ out) {
+    const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const uint64_t nt = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    for (uint64_t e = tid; e < n; e += nt) {
+        const uint64_t k = __ldg(keys + e);
+        const uint64_t y = ctr * k;
+        const uint64_t z = add64(y, k);
+        if constexpr (WIDE)
+            static_cast<uint64_t *>(out)[e] = squares64_yz(y, z);
+        else
+            static_cast<uint32_t *>(out)[e] = squares32_yz(y, z);
+    }
+}
+
+unsigned grid_for(uint64_t n, const void *fn) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const uint64_t full = static_cast<uint64_t>(current_sm_count()) * per_sm;
+    const uint64_t need = (n + 255) / 256;
+    return static_cast<unsigned>(need < full ? (need > 0 ? need : 1) : full);
+}
+
+}  // namespace
+
+cudaError_t launch_strided(bool wide, uint64_t key, uint64_t ctr_base, uint64_t stride, size_t n,
+                           void *out, cudaStream_t stream) {
+    if (n == 0) return cudaSuccess;
+    if (wide) {
+        strided_kernel<true><<<grid_for(n, reinterpret_cast<const void *>(&strided_kernel<true>)), 256, 0,
+                               stream>>>(key, ctr_base, stride, out, n);
+    } else {
+        strided_kernel<false><<<grid_for(n, reinterpret_cast<const void *>(&strided_kernel<false>)), 256, 0,
+                                stream>>>(key, ctr_base, stride, out, n);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_keys(bool wide, const uint64_t *keys, size_t n, uint64_t ctr, void *out,
+                        cudaStream_t stream) {
+    if (n == 0) return cudaSuccess;
+    if (wide) {
+        keys_kernel<true><<<grid_for(n, reinterpret_cast<const void *>(&keys_kernel<true>)), 256, 0, stream>>>(
+            keys, n, ctr, out);
+    } else {
+        keys_kernel<false><<<grid_for(n, reinterpret_cast<const void *>(&keys_kernel<false>)), 256, 0, stream>>>(
+            keys, n, ctr, out);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace sq

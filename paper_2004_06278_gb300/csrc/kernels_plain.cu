@@ -8,30 +8,48 @@
 // threads write adjacent chunks, so each warp store covers 32 * BYTES
 // contiguous bytes. The thread computes y = ctr*key once and then only adds:
 // within a chunk y_{j+1} = y_j + key, and z_j = y_{j+1}; between chunks
-// y += T * (counters per chunk) * key (Section 2's Weyl equivalence).
+// y += T * (counters per chunk) * key (Section 2's Weyl equivalence). Round
+// 1 squares y itself, and its value for consecutive counters follows a
+// second-order recurrence (see walk), so it costs additions, not multiplies.
 // Nothing is read from memory.
 #include <cuda_runtime.h>
 
 #include "internal.h"
-#include "squares_core.cuh"
+#include "squares_device.cuh"
+#include "stores.cuh"
 
 namespace sq {
 namespace {
 
-// Every op maps a chunk of consecutive counters to BYTES/4 32-bit words.
-// CPC = counters per chunk, EPC = output elements per counter.
+// Calls f(j, t, y, z) for the C consecutive counters of a chunk, where y and
+// z are the counter's Weyl terms and t its round-1 value. y starts at the
+// chunk's first counter, e = t(ctr+1) - t(ctr) there, c2 = 2*key^2: after
+// one squaring for t, each further counter costs three 64-bit additions
+// (y += key, t += e, e += c2) before rounds 2.. of the generator.
+template <int C, class F>
+__device__ __forceinline__ void walk(uint64_t y, uint64_t e, uint64_t key, uint64_t c2, F &&f) {
+    uint64_t t = round1_value(y);
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        const uint64_t z = add64(y, key);
+        f(j, t, y, z);
+        y = z;
+        t = add64(t, e);
+        e = add64(e, c2);
+    }
+}
+
+// Every op maps a chunk of consecutive counters to W 32-bit words.
+// EPC = output elements per counter.
 
 struct OpU32 {
     using T = uint32_t;
     static constexpr int EPC = 1;
     template <int W>
-    __device__ static void chunk(uint64_t y, uint64_t key, uint32_t (&w)[W]) {
-        uint64_t ys[W + 1];
-        ys[0] = y;
-#pragma unroll
-        for (int j = 0; j < W; ++j) ys[j + 1] = add64(ys[j], key);
-#pragma unroll
-        for (int j = 0; j < W; ++j) w[j] = squares32_yz(ys[j], ys[j + 1]);
+    __device__ static void chunk(uint64_t y, uint64_t e, uint64_t key, uint64_t c2, uint32_t (&w)[W]) {
+        walk<W>(y, e, key, c2, [&](int j, uint64_t t, uint64_t yy, uint64_t z) {
+            w[j] = squares32_tyz(t, yy, z);
+        });
     }
     __device__ static T single(uint64_t ctr0, uint64_t key, uint64_t e) {
         return squares32(ctr0 + e, key);
@@ -42,18 +60,12 @@ struct OpU64 {
     using T = uint64_t;
     static constexpr int EPC = 1;
     template <int W>
-    __device__ static void chunk(uint64_t y, uint64_t key, uint32_t (&w)[W]) {
-        constexpr int C = W / 2;
-        uint64_t ys[C + 1];
-        ys[0] = y;
-#pragma unroll
-        for (int j = 0; j < C; ++j) ys[j + 1] = add64(ys[j], key);
-#pragma unroll
-        for (int j = 0; j < C; ++j) {
-            const uint64_t v = squares64_yz(ys[j], ys[j + 1]);
+    __device__ static void chunk(uint64_t y, uint64_t e, uint64_t key, uint64_t c2, uint32_t (&w)[W]) {
+        walk<W / 2>(y, e, key, c2, [&](int j, uint64_t t, uint64_t yy, uint64_t z) {
+            const uint64_t v = squares64_tyz(t, yy, z);
             w[2 * j] = lo32(v);
             w[2 * j + 1] = hi32(v);
-        }
+        });
     }
     __device__ static T single(uint64_t ctr0, uint64_t key, uint64_t e) {
         return squares64(ctr0 + e, key);
@@ -64,13 +76,10 @@ struct OpUniformF32 {
     using T = float;
     static constexpr int EPC = 1;
     template <int W>
-    __device__ static void chunk(uint64_t y, uint64_t key, uint32_t (&w)[W]) {
-        uint64_t ys[W + 1];
-        ys[0] = y;
-#pragma unroll
-        for (int j = 0; j < W; ++j) ys[j + 1] = add64(ys[j], key);
-#pragma unroll
-        for (int j = 0; j < W; ++j) w[j] = __float_as_uint(uniform24(squares32_yz(ys[j], ys[j + 1])));
+    __device__ static void chunk(uint64_t y, uint64_t e, uint64_t key, uint64_t c2, uint32_t (&w)[W]) {
+        walk<W>(y, e, key, c2, [&](int j, uint64_t t, uint64_t yy, uint64_t z) {
+            w[j] = __float_as_uint(uniform24(squares32_tyz(t, yy, z)));
+        });
     }
     __device__ static T single(uint64_t ctr0, uint64_t key, uint64_t e) {
         return uniform24(squares32(ctr0 + e, key));
@@ -81,18 +90,13 @@ struct OpUniformBF16 {
     using T = uint16_t;
     static constexpr int EPC = 1;
     template <int W>
-    __device__ static void chunk(uint64_t y, uint64_t key, uint32_t (&w)[W]) {
-        constexpr int C = 2 * W;
-        uint64_t ys[C + 1];
-        ys[0] = y;
+    __device__ static void chunk(uint64_t y, uint64_t e, uint64_t key, uint64_t c2, uint32_t (&w)[W]) {
+        float f[2 * W];
+        walk<2 * W>(y, e, key, c2, [&](int j, uint64_t t, uint64_t yy, uint64_t z) {
+            f[j] = uniform24(squares32_tyz(t, yy, z));
+        });
 #pragma unroll
-        for (int j = 0; j < C; ++j) ys[j + 1] = add64(ys[j], key);
-#pragma unroll
-        for (int j = 0; j < W; ++j) {
-            const float a = uniform24(squares32_yz(ys[2 * j], ys[2 * j + 1]));
-            const float b = uniform24(squares32_yz(ys[2 * j + 1], ys[2 * j + 2]));
-            w[j] = pack_bf16_rz(a, b);
-        }
+        for (int j = 0; j < W; ++j) w[j] = pack_bf16_rz(f[2 * j], f[2 * j + 1]);
     }
     __device__ static T single(uint64_t ctr0, uint64_t key, uint64_t e) {
         return static_cast<T>(bf16_bits_rz(uniform24(squares32(ctr0 + e, key))));
@@ -103,19 +107,13 @@ struct OpNormalF32 {
     using T = float;
     static constexpr int EPC = 2;
     template <int W>
-    __device__ static void chunk(uint64_t y, uint64_t key, uint32_t (&w)[W]) {
-        constexpr int C = W / 2;
-        uint64_t ys[C + 1];
-        ys[0] = y;
-#pragma unroll
-        for (int j = 0; j < C; ++j) ys[j + 1] = add64(ys[j], key);
-#pragma unroll
-        for (int j = 0; j < C; ++j) {
-            const uint64_t v = squares64_yz(ys[j], ys[j + 1]);
-            const float2 z = box_muller(hi32(v), lo32(v));
-            w[2 * j] = __float_as_uint(z.x);
-            w[2 * j + 1] = __float_as_uint(z.y);
-        }
+    __device__ static void chunk(uint64_t y, uint64_t e, uint64_t key, uint64_t c2, uint32_t (&w)[W]) {
+        walk<W / 2>(y, e, key, c2, [&](int j, uint64_t t, uint64_t yy, uint64_t z) {
+            const uint64_t v = squares64_tyz(t, yy, z);
+            const float2 n = box_muller(hi32(v), lo32(v));
+            w[2 * j] = __float_as_uint(n.x);
+            w[2 * j + 1] = __float_as_uint(n.y);
+        });
     }
     __device__ static T single(uint64_t ctr0, uint64_t key, uint64_t e) {
         const uint64_t v = squares64(ctr0 + e / 2, key);
@@ -124,9 +122,49 @@ struct OpNormalF32 {
     }
 };
 
+// Two floats per squares64 output: the upper 32 bits, then the lower
+// (Section 5's split into halves), each as floor(half / 2^8) * 2^-24.
+struct OpUniform2F32 {
+    using T = float;
+    static constexpr int EPC = 2;
+    template <int W>
+    __device__ static void chunk(uint64_t y, uint64_t e, uint64_t key, uint64_t c2, uint32_t (&w)[W]) {
+        walk<W / 2>(y, e, key, c2, [&](int j, uint64_t t, uint64_t yy, uint64_t z) {
+            const uint64_t v = squares64_tyz(t, yy, z);
+            w[2 * j] = __float_as_uint(uniform24(hi32(v)));
+            w[2 * j + 1] = __float_as_uint(uniform24(lo32(v)));
+        });
+    }
+    __device__ static T single(uint64_t ctr0, uint64_t key, uint64_t e) {
+        const uint64_t v = squares64(ctr0 + e / 2, key);
+        return uniform24((e & 1) ? lo32(v) : hi32(v));
+    }
+};
+
+// 53-bit double uniforms floor(squares64 / 2^11) * 2^-53, built with
+// integer operations only (see uniform53_bits).
+struct OpUniformF64 {
+    using T = double;
+    static constexpr int EPC = 1;
+    template <int W>
+    __device__ static void chunk(uint64_t y, uint64_t e, uint64_t key, uint64_t c2, uint32_t (&w)[W]) {
+        walk<W / 2>(y, e, key, c2, [&](int j, uint64_t t, uint64_t yy, uint64_t z) {
+            const uint64_t b = uniform53_bits(squares64_tyz(t, yy, z));
+            w[2 * j] = lo32(b);
+            w[2 * j + 1] = hi32(b);
+        });
+    }
+    __device__ static T single(uint64_t ctr0, uint64_t key, uint64_t e) {
+        return __longlong_as_double(static_cast<long long>(uniform53_bits(squares64(ctr0 + e, key))));
+    }
+};
+
 template <int BYTES, bool CS>
 __device__ __forceinline__ void store_chunk(void *p, const uint32_t (&w)[BYTES / 4]) {
-    if constexpr (BYTES == 32) {
+    if constexpr (BYTES == 64) {
+        store32B<CS>(p, *reinterpret_cast<const uint32_t(*)[8]>(&w[0]));
+        store32B<CS>(static_cast<char *>(p) + 32, *reinterpret_cast<const uint32_t(*)[8]>(&w[8]));
+    } else if constexpr (BYTES == 32) {
         store32B<CS>(p, w);
     } else {
         store16B<CS>(p, w[0], w[1], w[2], w[3]);
@@ -153,22 +191,32 @@ __global__ void __launch_bounds__(512)
 
     // Counter of the first element of chunk `tid` (head is a multiple of EPC).
     uint64_t y = (ctr0 + (head + tid * EPV) / Op::EPC) * key;
+    const uint64_t c2 = (key * key) << 1;
+    uint64_t e = round1_delta(y, key);
+    // Between chunks the counter jumps by nthreads*CPV: y by that many keys,
+    // e (linear in the counter) by that many c2.
     const uint64_t ystep = nthreads * CPV * key;
+    const uint64_t estep = nthreads * CPV * c2;
     char *p = reinterpret_cast<char *>(out + head) + tid * BYTES;
     const uint64_t pstep = nthreads * BYTES;
     for (uint64_t it = (nvec - tid + nthreads - 1) / nthreads; it != 0; --it) {
         uint32_t w[W];
-        Op::template chunk<W>(y, key, w);
+        Op::template chunk<W>(y, e, key, c2, w);
         store_chunk<BYTES, CS>(p, w);
         y = add64(y, ystep);
+        e = add64(e, estep);
         p += pstep;
     }
 }
 
-// Variants: 0 = 32 B stores, 1 = 32 B streaming stores, 2 = 16 B stores,
-// 3 = 16 B streaming stores.
-constexpr int kPlainVariants = 4;
-const char *kPlainVariantNames[kPlainVariants] = {"st32", "st32.cs", "st16", "st16.cs"};
+// Variants (bytes written per thread per step, cache policy):
+// 0 = 32 B, 1 = 32 B streaming, 2 = 16 B, 3 = 16 B streaming,
+// 4 = 64 B (two adjacent 32 B stores), 5 = 64 B streaming.
+constexpr int kPlainVariants = 6;
+const char *kPlainVariantNames[kPlainVariants] = {"st32", "st32.cs", "st16", "st16.cs",
+                                                  "st32x2", "st32x2.cs"};
+
+constexpr int variant_bytes(int v) { return v < 2 ? 32 : (v < 4 ? 16 : 64); }
 
 template <class Op>
 const void *plain_fn(int variant) {
@@ -176,7 +224,9 @@ const void *plain_fn(int variant) {
         case 0: return reinterpret_cast<const void *>(&plain_kernel<Op, 32, false>);
         case 1: return reinterpret_cast<const void *>(&plain_kernel<Op, 32, true>);
         case 2: return reinterpret_cast<const void *>(&plain_kernel<Op, 16, false>);
-        default: return reinterpret_cast<const void *>(&plain_kernel<Op, 16, true>);
+        case 3: return reinterpret_cast<const void *>(&plain_kernel<Op, 16, true>);
+        case 4: return reinterpret_cast<const void *>(&plain_kernel<Op, 64, false>);
+        default: return reinterpret_cast<const void *>(&plain_kernel<Op, 64, true>);
     }
 }
 
@@ -187,6 +237,8 @@ const void *plain_fn_for(int kernel_id, int variant) {
         case SQ_KERNEL_UNIFORM_F32: return plain_fn<OpUniformF32>(variant);
         case SQ_KERNEL_UNIFORM_BF16: return plain_fn<OpUniformBF16>(variant);
         case SQ_KERNEL_NORMAL_F32: return plain_fn<OpNormalF32>(variant);
+        case SQ_KERNEL_UNIFORM2_F32: return plain_fn<OpUniform2F32>(variant);
+        case SQ_KERNEL_UNIFORM_F64: return plain_fn<OpUniformF64>(variant);
         default: return nullptr;
     }
 }
@@ -195,10 +247,11 @@ template <class Op>
 cudaError_t launch_op(const Cfg &cfg, uint64_t key, uint64_t ctr0, size_t n, void *out,
                       cudaStream_t stream, int max_ctas) {
     using T = typename Op::T;
-    const int bytes = (cfg.variant < 2) ? 32 : 16;
+    const int bytes = variant_bytes(cfg.variant);
+    const int align = bytes > 32 ? 32 : bytes;  // each store is at most 32 B
     const size_t epv = bytes / sizeof(T);
     const uintptr_t addr = reinterpret_cast<uintptr_t>(out);
-    size_t head = ((bytes - (addr % bytes)) % bytes) / sizeof(T);
+    size_t head = ((align - (addr % align)) % align) / sizeof(T);
     if (head > n) head = n;
     if (head % Op::EPC != 0) head = n;  // pairs would straddle chunks: all singles
     const size_t nvec = (n - head) / epv;
@@ -214,7 +267,9 @@ cudaError_t launch_op(const Cfg &cfg, uint64_t key, uint64_t ctr0, size_t n, voi
         case 0: plain_kernel<Op, 32, false><<<grid, cfg.block, 0, stream>>>(key, ctr0, o, n, head, nvec); break;
         case 1: plain_kernel<Op, 32, true><<<grid, cfg.block, 0, stream>>>(key, ctr0, o, n, head, nvec); break;
         case 2: plain_kernel<Op, 16, false><<<grid, cfg.block, 0, stream>>>(key, ctr0, o, n, head, nvec); break;
-        default: plain_kernel<Op, 16, true><<<grid, cfg.block, 0, stream>>>(key, ctr0, o, n, head, nvec); break;
+        case 3: plain_kernel<Op, 16, true><<<grid, cfg.block, 0, stream>>>(key, ctr0, o, n, head, nvec); break;
+        case 4: plain_kernel<Op, 64, false><<<grid, cfg.block, 0, stream>>>(key, ctr0, o, n, head, nvec); break;
+        default: plain_kernel<Op, 64, true><<<grid, cfg.block, 0, stream>>>(key, ctr0, o, n, head, nvec); break;
     }
     return cudaGetLastError();
 }
@@ -249,6 +304,10 @@ cudaError_t launch_plain(int kernel_id, const Cfg &cfg, uint64_t key, uint64_t c
             return launch_op<OpUniformBF16>(cfg, key, ctr_base, n, out, stream, max_ctas);
         case SQ_KERNEL_NORMAL_F32:
             return launch_op<OpNormalF32>(cfg, key, ctr_base, n, out, stream, max_ctas);
+        case SQ_KERNEL_UNIFORM2_F32:
+            return launch_op<OpUniform2F32>(cfg, key, ctr_base, n, out, stream, max_ctas);
+        case SQ_KERNEL_UNIFORM_F64:
+            return launch_op<OpUniformF64>(cfg, key, ctr_base, n, out, stream, max_ctas);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -58,7 +58,8 @@ def test_make_keys_errors(lib):
 
 
 @pytest.mark.parametrize("fn,elem", [(sq.sq_u32, 4), (sq.sq_u64, 8), (sq.sq_uniform_f32, 4),
-                                     (sq.sq_uniform_bf16, 2), (sq.sq_normal_f32, 4)])
+                                     (sq.sq_uniform_bf16, 2), (sq.sq_normal_f32, 4),
+                                     (sq.sq_uniform2_f32, 4), (sq.sq_uniform_f64, 8)])
 def test_plain_argument_checks(lib, fn, elem):
     fn(1, 0, 0, 0)  # n = 0: no launch, OK
     with pytest.raises(sq.SquaresError) as e:
@@ -71,6 +72,25 @@ def test_plain_argument_checks(lib, fn, elem):
     with pytest.raises(sq.SquaresError) as e:
         fn(1, 0, (1 << 62) + 1, 0x1000)
     assert e.value.status == sq.SQ_ERANGE
+
+
+def test_strided_and_keys_argument_checks(lib):
+    for fn, elem in ((sq.sq_u32_strided, 4), (sq.sq_u64_strided, 8)):
+        fn(1, 0, 3, 0, 0)
+        with pytest.raises(sq.SquaresError) as e:
+            fn(1, 0, 3, 10, 0)
+        assert e.value.status == sq.SQ_EINVAL
+        with pytest.raises(sq.SquaresError) as e:
+            fn(1, 0, 3, 10, 0x1000 + elem // 2)
+        assert e.value.status == sq.SQ_EINVAL
+    for fn in (sq.sq_keys_u32, sq.sq_keys_u64):
+        fn(0, 0, 5, 0)
+        with pytest.raises(sq.SquaresError) as e:
+            fn(0, 4, 5, 0x1000)
+        assert e.value.status == sq.SQ_EINVAL
+        with pytest.raises(sq.SquaresError) as e:
+            fn(0x1004, 4, 5, 0x1000)
+        assert e.value.status == sq.SQ_EINVAL
 
 
 def test_batch_and_fused_argument_checks(lib):
@@ -96,7 +116,8 @@ def test_batch_and_fused_argument_checks(lib):
 
 
 def test_config_table(lib):
-    assert sq.sq_num_variants(sq.SQ_KERNEL_U32) == 4
+    assert sq.sq_num_variants(sq.SQ_KERNEL_U32) == 6
+    assert sq.sq_num_variants(sq.SQ_KERNEL_BATCH) == 4
     assert sq.sq_variant_name(sq.SQ_KERNEL_U32, 0) == "st32"
     assert sq.sq_variant_name(sq.SQ_KERNEL_U32, 99) is None
     cfg = sq.sq_get_config(sq.SQ_KERNEL_U64, 1 << 20)

@@ -112,3 +112,36 @@ def test_fused_stats_against_numpy():
         assert int(s[i]) == int((v >> 24).astype(np.uint64).sum())
     allv = np.concatenate(allv)
     assert np.array_equal(h, np.bincount(allv >> 24, minlength=256).astype(np.uint64))
+
+
+def test_strided_is_subsampled_stream():
+    """Counters base + i*stride: the same values as every stride-th output of
+    the consecutive stream (and key-counter mode is stride 0 of pairs)."""
+    k = key()
+    base = (1 << 64) - 50
+    for stride in (1, 3, 7):
+        n = 1000
+        assert np.array_equal(oracle.fill32_strided(k, base, stride, n),
+                              oracle.fill32(k, base, n * stride)[::stride])
+        assert np.array_equal(oracle.fill64_strided(k, base, stride, n),
+                              oracle.fill64(k, base, n * stride)[::stride])
+    same = oracle.fill32_strided(k, 99, 0, 5)
+    assert np.all(same == oracle.squares32(99, k))
+
+
+def test_uniform2_halves_against_numpy():
+    n = 2001
+    v = oracle.fill64(key(), 3, (n + 1) // 2)
+    halves = np.stack([v >> np.uint64(32), v & np.uint64(0xFFFFFFFF)], axis=1).reshape(-1)[:n]
+    expect = (halves >> np.uint64(8)).astype(np.float32) * np.float32(2.0 ** -24)
+    assert np.array_equal(oracle.uniform2_f32(key(), 3, n), expect)
+
+
+def test_uniform_f64_against_numpy():
+    n = 5000
+    v = oracle.fill64(key(), 11, n)
+    expect = (v >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    got = oracle.uniform_f64(key(), 11, n)
+    assert np.array_equal(got, expect)
+    assert got.min() >= 0 and got.max() < 1
+    assert np.all(np.floor(got * 2.0 ** 53) == got * 2.0 ** 53)
