@@ -136,7 +136,7 @@ int sq_batch_validate(const int64_t *lengths, const int64_t *offsets, size_t nst
  *                  out[2j] = r cos theta, out[2j+1] = r sin theta; an odd n
  *                  drops the last sine. Computed in FP32 with ln u1 taken
  *                  through log1p of the exact integer complement when
- *                  u1 >= 1/2. Error against the FP64 values: at most 2e-6
+ *                  1 - u1 < 2^-7. Error against the FP64 values: at most 2e-6
  *                  absolute where |z| < 5 and 1e-5 relative beyond.
  * out [device], naturally aligned. Errors as for sq_u32.
  * ---------------------------------------------------------------------- */

@@ -128,7 +128,7 @@ __device__ __forceinline__ void boundary_chunk(const uint64_t *__restrict__ keys
 // EPV consecutive outputs per thread per tile: 8 (one 32-byte store) or 16
 // (two adjacent 32-byte stores).
 template <bool CS, int EPV>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(512, 4)
     batch_kernel(const uint64_t *__restrict__ keys, const uint64_t *__restrict__ bases,
                  const int64_t *__restrict__ lengths, const int64_t *__restrict__ offsets,
                  uint32_t S, uint32_t *__restrict__ out, uint32_t head) {

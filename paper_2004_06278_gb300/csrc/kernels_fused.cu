@@ -60,8 +60,27 @@ __global__ void __launch_bounds__(512)
         const uint64_t c2 = (key * key) << 1;
         uint32_t x = 0, sum = 0;
         const uint64_t cnt = (lb > la) ? lb - la : 0;
-#pragma unroll 4
-        for (uint64_t i = 0; i < cnt; ++i) {
+        // Blocks of 8 counters: t_{j+1} = t_j + e + j*c2 with e fixed for the
+        // block (one three-input addition per value), e += 8*c2 per block.
+        uint64_t jc2[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) jc2[j] = c2 * static_cast<uint64_t>(j);
+        const uint64_t c2x8 = c2 << 3;
+        uint64_t i = 0;
+        for (; i + 8 <= cnt; i += 8) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const uint64_t yn = add64(y, key);
+                const uint32_t u = squares32_tyz(t, y, yn);
+                y = yn;
+                t = add64x3(t, er, jc2[j]);
+                x ^= u;
+                sum += u >> 24;
+                atomicAdd(h + (u >> 24), 1u);
+            }
+            er = add64(er, c2x8);
+        }
+        for (; i < cnt; ++i) {
             const uint64_t yn = add64(y, key);
             const uint32_t u = squares32_tyz(t, y, yn);
             y = yn;

@@ -24,8 +24,9 @@ namespace {
 // Calls f(j, t, y, z) for the C consecutive counters of a chunk, where y and
 // z are the counter's Weyl terms and t its round-1 value. y starts at the
 // chunk's first counter, e = t(ctr+1) - t(ctr) there, c2 = 2*key^2: after
-// one squaring for t, each further counter costs three 64-bit additions
-// (y += key, t += e, e += c2) before rounds 2.. of the generator.
+// one squaring for t, counter j+1 follows from counter j by y += key and
+// t += e + j*c2 (one three-input addition; j*c2 is the same for every thread
+// of the launch, since the key is) before rounds 2.. of the generator.
 template <int C, class F>
 __device__ __forceinline__ void walk(uint64_t y, uint64_t e, uint64_t key, uint64_t c2, F &&f) {
     uint64_t t = round1_value(y);
@@ -34,8 +35,7 @@ __device__ __forceinline__ void walk(uint64_t y, uint64_t e, uint64_t key, uint6
         const uint64_t z = add64(y, key);
         f(j, t, y, z);
         y = z;
-        t = add64(t, e);
-        e = add64(e, c2);
+        t = add64x3(t, e, c2 * static_cast<uint64_t>(j));
     }
 }
 

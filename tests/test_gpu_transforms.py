@@ -62,14 +62,16 @@ def test_normal_within_bounds(gpu_lib, n):
 
 def test_normal_edge_integers(gpu_lib):
     """Counters whose squares64 outputs have hi near 0 (deep tail), near
-    2^31 (the switch to log1p) and near 2^32 - 1 (u1 -> 1, r -> 0): found by
-    scanning the oracle's outputs, then generated on the GPU."""
+    2^32 - 2^25 (the switch from log to log1p, 1 - u1 = 2^-7) and near
+    2^32 - 1 (u1 -> 1, r -> 0): found by scanning the oracle's outputs, then
+    generated on the GPU."""
     key = int(gpu_lib.make_keys(11, 1)[0])
     n_pairs = 1 << 24
     v = oracle.fill64(key, 0, n_pairs)
     hi = v >> np.uint64(32)
+    switch = (1 << 32) - 1 - (1 << 25)
     picks = np.concatenate([np.argsort(hi)[:64], np.argsort(hi)[-64:],
-                            np.argsort(np.abs(hi.astype(np.int64) - (1 << 31)))[:64]])
+                            np.argsort(np.abs(hi.astype(np.int64) - switch))[:64]])
     for j in picks:
         j = int(j)
         got = _run(C.sq_normal_f32, 4, np.float32, key, j, 2)
@@ -96,7 +98,7 @@ def test_transform_variants(gpu_lib):
     wb = oracle.uniform_bf16(key, 3, n)
     wn = oracle.normal_f64(key, 3, n)
     try:
-        for v in range(4):
+        for v in range(C.sq_num_variants(C.SQ_KERNEL_UNIFORM_F32)):
             for block in (128, 512):
                 for kid in (C.SQ_KERNEL_UNIFORM_F32, C.SQ_KERNEL_UNIFORM_BF16, C.SQ_KERNEL_NORMAL_F32):
                     C.sq_set_config(kid, 0, v, block, 0)
