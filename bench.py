@@ -69,6 +69,8 @@ def parse_args():
                                          "normal_f32", "uniform2_f32", "uniform_f64", "fused"],
                    help="run one kernel on a small case (for ncu) instead of the benchmark")
     p.add_argument("--profile-n", type=int, default=1 << 28)
+    p.add_argument("--reference-budget-s", type=float, default=60.0,
+                   help="wall time the reference arm aims to spend on its K steps")
     return p.parse_args()
 
 
@@ -197,8 +199,8 @@ def reference_arm(args, rank, world):
     minute."""
     if rank != 0:
         return 0
-    rate, _, threads = oracle_sample_rate(1 << 24, 1 << 26)  # calibration / warm-up
-    budget_s = 60.0
+    rate, _, threads = oracle_sample_rate(1 << 20, 1 << 22)  # calibration / warm-up
+    budget_s = args.reference_budget_s
     per_step = rate * budget_s / max(1, args.steps)
     unit = 5 << 20  # 2^20 squares64 + 2^22 squares32
     units = int(max(1, min((N64 + N32) // unit, per_step // unit)))
