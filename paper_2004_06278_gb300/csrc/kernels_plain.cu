@@ -209,14 +209,88 @@ __global__ void __launch_bounds__(512)
     }
 }
 
+// TMA bulk-store body: each warp stages 32 lanes x 64 bytes (2 KiB of
+// consecutive output) in shared memory, double-buffered, and one lane hands
+// each full buffer to the copy engine with cp.async.bulk (shared -> global).
+// The lane waits with cp.async.bulk.wait_group.read until the copy issued
+// two steps earlier has finished reading a buffer before the warp refills
+// it, and waits for all of its copies before the CTA exits. The warp
+// chunks cover [head, head + nwc * 2 KiB / sizeof(T)); the rest is written
+// element by element.
+constexpr int kBulkLaneBytes = 64;
+constexpr int kBulkWarpBytes = 32 * kBulkLaneBytes;
+
+template <class Op>
+__global__ void __launch_bounds__(512)
+    plain_bulk_kernel(uint64_t key, uint64_t ctr0, typename Op::T *__restrict__ out, uint64_t n,
+                      uint64_t head, uint64_t nwc) {
+    using T = typename Op::T;
+    constexpr int W = kBulkLaneBytes / 4;
+    constexpr int EPV = kBulkLaneBytes / sizeof(T);
+    constexpr int CPV = EPV / Op::EPC;
+    constexpr int WC_ELEMS = 32 * EPV;
+    extern __shared__ __align__(128) unsigned char stage_all[];
+    const int lane = threadIdx.x & 31;
+    const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const uint64_t nthreads = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+
+    const uint64_t tail0 = head + nwc * WC_ELEMS;
+    for (uint64_t e = tid; e < head; e += nthreads) out[e] = Op::single(ctr0, key, e);
+    for (uint64_t e = tail0 + tid; e < n; e += nthreads) out[e] = Op::single(ctr0, key, e);
+
+    const uint64_t gwarp = tid >> 5;
+    const uint64_t nwarps = nthreads >> 5;
+    if (gwarp >= nwc) return;  // uniform across the warp
+
+    const uint32_t stage = static_cast<uint32_t>(__cvta_generic_to_shared(
+        stage_all + (threadIdx.x >> 5) * 2 * kBulkWarpBytes));
+    uint64_t y = (ctr0 + (head + gwarp * WC_ELEMS + lane * EPV) / Op::EPC) * key;
+    const uint64_t c2 = (key * key) << 1;
+    uint64_t e = round1_delta(y, key);
+    const uint64_t ystep = nwarps * 32 * CPV * key;
+    const uint64_t estep = nwarps * 32 * CPV * c2;
+    char *gp = reinterpret_cast<char *>(out + head) + gwarp * kBulkWarpBytes;
+    const uint64_t gstep = nwarps * kBulkWarpBytes;
+    uint32_t buf = 0;
+    for (uint64_t c = gwarp; c < nwc; c += nwarps) {
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+        __syncwarp();
+        uint32_t w[W];
+        Op::template chunk<W>(y, e, key, c2, w);
+        const uint32_t s = stage + buf * kBulkWarpBytes + lane * kBulkLaneBytes;
+#pragma unroll
+        for (int q = 0; q < W / 4; ++q)
+            asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(s + 16 * q), "r"(w[4 * q]),
+                         "r"(w[4 * q + 1]), "r"(w[4 * q + 2]), "r"(w[4 * q + 3])
+                         : "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+            asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gp),
+                         "r"(stage + buf * kBulkWarpBytes), "n"(kBulkWarpBytes)
+                         : "memory");
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        }
+        y = add64(y, ystep);
+        e = add64(e, estep);
+        gp += gstep;
+        buf ^= 1u;
+    }
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
 // Variants (bytes written per thread per step, cache policy):
 // 0 = 32 B, 1 = 32 B streaming, 2 = 16 B, 3 = 16 B streaming,
-// 4 = 64 B (two adjacent 32 B stores), 5 = 64 B streaming.
-constexpr int kPlainVariants = 6;
+// 4 = 64 B (two adjacent 32 B stores), 5 = 64 B streaming,
+// 6 = 64 B per lane staged in shared memory, TMA bulk store per warp.
+constexpr int kPlainVariants = 7;
+constexpr int kBulkVariant = 6;
 const char *kPlainVariantNames[kPlainVariants] = {"st32", "st32.cs", "st16", "st16.cs",
-                                                  "st32x2", "st32x2.cs"};
+                                                  "st32x2", "st32x2.cs", "bulk64"};
 
 constexpr int variant_bytes(int v) { return v < 2 ? 32 : (v < 4 ? 16 : 64); }
+
+size_t bulk_smem(int block) { return static_cast<size_t>(block / 32) * 2 * kBulkWarpBytes; }
 
 template <class Op>
 const void *plain_fn(int variant) {
@@ -226,8 +300,19 @@ const void *plain_fn(int variant) {
         case 2: return reinterpret_cast<const void *>(&plain_kernel<Op, 16, false>);
         case 3: return reinterpret_cast<const void *>(&plain_kernel<Op, 16, true>);
         case 4: return reinterpret_cast<const void *>(&plain_kernel<Op, 64, false>);
-        default: return reinterpret_cast<const void *>(&plain_kernel<Op, 64, true>);
+        case 5: return reinterpret_cast<const void *>(&plain_kernel<Op, 64, true>);
+        default: return reinterpret_cast<const void *>(&plain_bulk_kernel<Op>);
     }
+}
+
+// The bulk body needs up to 64 KiB of dynamic shared memory (block 512):
+// opt in once per instantiation.
+template <class Op>
+cudaError_t prepare_bulk() {
+    static cudaError_t status = cudaFuncSetAttribute(
+        reinterpret_cast<const void *>(&plain_bulk_kernel<Op>),
+        cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bulk_smem(512)));
+    return status;
 }
 
 const void *plain_fn_for(int kernel_id, int variant) {
@@ -244,9 +329,54 @@ const void *plain_fn_for(int kernel_id, int variant) {
 }
 
 template <class Op>
+int plain_max_ctas_per_sm_op(int variant, int block) {
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, plain_fn<Op>(variant), block, 0) !=
+        cudaSuccess)
+        return 1;
+    return blocks > 0 ? blocks : 1;
+}
+
+template <class Op>
+cudaError_t launch_bulk(const Cfg &cfg, uint64_t key, uint64_t ctr0, size_t n, void *out,
+                        cudaStream_t stream, int max_ctas) {
+    using T = typename Op::T;
+    const cudaError_t prep = prepare_bulk<Op>();
+    if (prep != cudaSuccess) return prep;
+    const size_t wc_elems = 32 * kBulkLaneBytes / sizeof(T);
+    const uintptr_t addr = reinterpret_cast<uintptr_t>(out);
+    size_t head = ((32 - (addr % 32)) % 32) / sizeof(T);
+    if (head > n) head = n;
+    if (head % Op::EPC != 0) head = n;
+    const size_t nwc = (n - head) / wc_elems;
+    const int ctas = cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : max_ctas;
+    uint64_t grid = static_cast<uint64_t>(current_sm_count()) * (ctas > 0 ? ctas : 1);
+    const uint64_t warps_per_cta = cfg.block / 32;
+    const uint64_t need = (nwc + warps_per_cta - 1) / warps_per_cta;
+    const uint64_t need_single = (head + (n - head - nwc * wc_elems) + cfg.block - 1) / cfg.block;
+    const uint64_t want = need > need_single ? need : need_single;
+    if (grid > want) grid = want > 0 ? want : 1;
+    plain_bulk_kernel<Op><<<grid, cfg.block, bulk_smem(cfg.block), stream>>>(
+        key, ctr0, static_cast<T *>(out), n, head, nwc);
+    return cudaGetLastError();
+}
+
+template <class Op>
 cudaError_t launch_op(const Cfg &cfg, uint64_t key, uint64_t ctr0, size_t n, void *out,
                       cudaStream_t stream, int max_ctas) {
     using T = typename Op::T;
+    if (cfg.variant == kBulkVariant) {
+        // The copy engine path is used for device memory only; anything else
+        // (pinned or managed host memory) takes the direct 64-byte stores.
+        cudaPointerAttributes attr;
+        if (cudaPointerGetAttributes(&attr, out) == cudaSuccess && attr.type == cudaMemoryTypeDevice)
+            return launch_bulk<Op>(cfg, key, ctr0, n, out, stream, max_ctas);
+        cudaGetLastError();
+        Cfg direct = cfg;
+        direct.variant = 4;
+        const int mc = cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : plain_max_ctas_per_sm_op<Op>(4, cfg.block);
+        return launch_op<Op>(direct, key, ctr0, n, out, stream, mc);
+    }
     const int bytes = variant_bytes(cfg.variant);
     const int align = bytes > 32 ? 32 : bytes;  // each store is at most 32 B
     const size_t epv = bytes / sizeof(T);
@@ -285,7 +415,13 @@ const char *plain_variant_name(int variant) {
 int plain_max_ctas_per_sm(int kernel_id, int variant, int block) {
     const void *fn = plain_fn_for(kernel_id, variant);
     int blocks = 0;
-    if (!fn || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, block, 0) != cudaSuccess)
+    const size_t smem = variant == kBulkVariant ? bulk_smem(block) : 0;
+    if (variant == kBulkVariant) {
+        // the opt-in must precede the occupancy query for > 48 KiB
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(bulk_smem(512)));
+    }
+    if (!fn || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, block, smem) != cudaSuccess)
         return 1;
     return blocks > 0 ? blocks : 1;
 }

@@ -120,3 +120,29 @@ def test_async_on_torch_stream(gpu_lib):
         gpu_lib.u32(key, 5, n, out=out)
     s.synchronize()
     assert np.array_equal(out.cpu().numpy(), oracle.fill32(key, 5, n))
+
+
+def test_bulk_variant_device_and_host_memory(gpu_lib):
+    """The shared-memory + bulk-copy variant on device memory, and its
+    fallback to direct stores when the output is pinned host memory."""
+    import torch
+
+    key = int(gpu_lib.make_keys(10, 1)[0])
+    bulk = [v for v in range(C.sq_num_variants(C.SQ_KERNEL_U32))
+            if C.sq_variant_name(C.SQ_KERNEL_U32, v) == "bulk64"][0]
+    n = 3 * 152 * 16 * 512 + 21
+    try:
+        for kid, fn, dt, ref in ((C.SQ_KERNEL_U32, C.sq_u32, torch.int32, oracle.fill32),
+                                 (C.SQ_KERNEL_U64, C.sq_u64, torch.int64, oracle.fill64)):
+            C.sq_set_config(kid, 0, bulk, 256, 0)
+            want = ref(key, 11, n)
+            for off in (0, 1, 3):
+                elem = 4 if dt == torch.int32 else 8
+                assert np.array_equal(_run(fn, elem, key, 11, n, off), want), off
+            host = torch.empty(n, dtype=dt, pin_memory=True)
+            fn(key, 11, n, host.data_ptr(), stream_handle())
+            torch.cuda.synchronize()
+            assert np.array_equal(host.numpy().view(want.dtype), want)
+    finally:
+        C.sq_set_config(C.SQ_KERNEL_U32, 0, 0, 256, 0)
+        C.sq_set_config(C.SQ_KERNEL_U64, 0, 0, 256, 0)
