@@ -50,6 +50,13 @@ const char *sq_last_error(void);
 /* Version of this ABI: 100 * major + minor. */
 int sq_abi_version(void);
 
+/* Test hook: the next call of the named entry point (e.g. "sq_u32") on the
+ * calling thread fails with SQ_ECUDA after its argument checks and before it
+ * touches the GPU, as a failed launch would; NULL or "" disarms. Lets a
+ * caller exercise its error handling without faulting a device. No
+ * counterpart in the paper. */
+int sq_debug_fail_next(const char *entry_point);
+
 /* ------------------------------------------------------------------------
  * Keys (Section 3, "different digits"; Section 4, keys.h).
  * Writes n distinct keys to keys[0..n) [host]. Each key's upper eight hex

@@ -55,6 +55,7 @@ _i = ctypes.c_int
 # name -> argument types; every entry point returns int status unless noted.
 _SIGNATURES = {
     "sq_make_keys": [_u64, _sz, _p],
+    "sq_debug_fail_next": [ctypes.c_char_p],
     "sq_u32": [_u64, _u64, _sz, _p, _p],
     "sq_u64": [_u64, _u64, _sz, _p, _p],
     "sq_u32_strided": [_u64, _u64, _u64, _sz, _p, _p],
@@ -133,6 +134,10 @@ def sq_last_error() -> str:
 
 def sq_abi_version() -> int:
     return int(load().sq_abi_version())
+
+
+def sq_debug_fail_next(entry_point: str | None) -> None:
+    _call("sq_debug_fail_next", entry_point.encode() if entry_point else None)
 
 
 def sq_make_keys(seed: int, n: int, keys_ptr: int) -> None:

@@ -19,6 +19,7 @@
 namespace {
 
 thread_local std::string g_error;
+thread_local std::string g_fail_next;  // armed by sq_debug_fail_next
 
 int fail(int code, const char *fmt, ...) {
     char buf[512];
@@ -40,6 +41,17 @@ int ok() {
 }
 
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// True once if sq_debug_fail_next armed a failure for this entry point.
+bool injected(const char *name) {
+    if (g_fail_next.empty() || g_fail_next != name) return false;
+    g_fail_next.clear();
+    return true;
+}
+
+int injected_fail(const char *name) {
+    return fail(SQ_ECUDA, "%s: injected launch failure (sq_debug_fail_next)", name);
+}
 
 constexpr size_t kMaxElems = size_t(1) << 62;
 constexpr size_t kMaxStreams = size_t(1) << 31;
@@ -113,6 +125,7 @@ int plain_entry(int kid, uint64_t key, uint64_t base, size_t n, void *out, size_
     if (out == nullptr) return fail(SQ_EINVAL, "%s: out is NULL with n = %zu", name, n);
     if (!aligned(out, elem)) return fail(SQ_EINVAL, "%s: out is not %zu-byte aligned", name, elem);
     if (n > kMaxElems) return fail(SQ_ERANGE, "%s: n = %zu exceeds 2^62", name, n);
+    if (injected(name)) return injected_fail(name);
     const sq::Cfg cfg = table().get(kid, n);
     const cudaError_t e = sq::launch_plain(kid, cfg, key, base, n, out, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, name);
@@ -158,6 +171,11 @@ extern "C" {
 const char *sq_last_error(void) { return g_error.c_str(); }
 
 int sq_abi_version(void) { return 100; }
+
+int sq_debug_fail_next(const char *entry_point) {
+    g_fail_next = entry_point ? entry_point : "";
+    return ok();
+}
 
 int sq_make_keys(uint64_t seed, size_t n, uint64_t *keys) {
     if (n > kMaxStreams) return fail(SQ_ERANGE, "sq_make_keys: n = %zu exceeds 2^31", n);
@@ -206,6 +224,7 @@ static int strided_entry(bool wide, uint64_t key, uint64_t base, uint64_t stride
     if (out == nullptr) return fail(SQ_EINVAL, "%s: out is NULL with n = %zu", name, n);
     if (!aligned(out, elem)) return fail(SQ_EINVAL, "%s: out is not %zu-byte aligned", name, elem);
     if (n > kMaxElems) return fail(SQ_ERANGE, "%s: n = %zu exceeds 2^62", name, n);
+    if (injected(name)) return injected_fail(name);
     const cudaError_t e = sq::launch_strided(wide, key, base, stride, n, out, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, name);
     return ok();
@@ -228,6 +247,7 @@ static int keys_entry(bool wide, const uint64_t *keys, size_t n, uint64_t ctr, v
     if (!keys || !out) return fail(SQ_EINVAL, "%s: NULL array with nkeys = %zu", name, n);
     if (!aligned(keys, 8) || !aligned(out, elem)) return fail(SQ_EINVAL, "%s: misaligned array", name);
     if (n > kMaxElems) return fail(SQ_ERANGE, "%s: nkeys = %zu exceeds 2^62", name, n);
+    if (injected(name)) return injected_fail(name);
     const cudaError_t e = sq::launch_keys(wide, keys, n, ctr, out, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, name);
     return ok();
@@ -246,6 +266,7 @@ int sq_batch(const uint64_t *keys, const uint64_t *ctr_bases, const int64_t *len
     if (nstreams == 0) return ok();
     const int rc = batch_checks(keys, ctr_bases, lengths, offsets, nstreams, out, "sq_batch");
     if (rc != SQ_OK) return rc;
+    if (injected("sq_batch")) return injected_fail("sq_batch");
     const sq::Cfg cfg = table().get(SQ_KERNEL_BATCH, 0);
     const cudaError_t e = sq::launch_batch(cfg, keys, ctr_bases, lengths, offsets, nstreams, out,
                                            static_cast<cudaStream_t>(stream));
@@ -288,6 +309,7 @@ int sq_fused_stats(const uint64_t *keys, const uint64_t *ctr_bases, size_t nstre
     if (!aligned(hist256, 8) || (nstreams > 0 && (!aligned(keys, 8) || !aligned(ctr_bases, 8) ||
                                                   !aligned(xor_out, 4) || !aligned(sum_top, 8))))
         return fail(SQ_EINVAL, "sq_fused_stats: misaligned array");
+    if (injected("sq_fused_stats")) return injected_fail("sq_fused_stats");
     const sq::Cfg cfg = table().get(SQ_KERNEL_FUSED, nstreams * ctrs_per_stream);
     const cudaError_t e = sq::launch_fused(cfg, keys, ctr_bases, nstreams, ctrs_per_stream, xor_out,
                                            sum_top, hist256, static_cast<cudaStream_t>(stream));
@@ -623,6 +645,7 @@ int sq_batch_graph_create(const uint64_t *keys, const uint64_t *ctr_bases, const
 
 int sq_graph_launch(sq_graph_t graph, sq_stream_t stream) {
     if (!graph) return fail(SQ_EINVAL, "sq_graph_launch: graph is NULL");
+    if (injected("sq_graph_launch")) return injected_fail("sq_graph_launch");
     const cudaError_t e = cudaGraphLaunch(graph->exec, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "sq_graph_launch");
     return ok();

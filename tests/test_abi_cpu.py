@@ -154,3 +154,26 @@ def test_last_error_is_per_call(lib):
     assert "NULL" in sq.sq_last_error()
     sq.sq_u32(1, 0, 0, 0)
     assert sq.sq_last_error() == ""
+
+
+def test_injected_launch_failure_reaches_the_caller(lib):
+    """A failed launch surfaces as SQ_ECUDA with a message, through the C ABI
+    and the binding; made on the host (no GPU is touched: the armed entry
+    point fails after its argument checks and before any CUDA call)."""
+    calls = [("sq_u32", lambda: sq.sq_u32(1, 0, 16, 0x1000)),
+             ("sq_u64_strided", lambda: sq.sq_u64_strided(1, 0, 3, 16, 0x1000)),
+             ("sq_keys_u32", lambda: sq.sq_keys_u32(0x1000, 4, 0, 0x2000)),
+             ("sq_batch", lambda: sq.sq_batch(0x1000, 0x1000, 0x1000, 0x1000, 3, 0x1000)),
+             ("sq_fused_stats", lambda: sq.sq_fused_stats(0x1000, 0x1000, 4, 16, 0x1000, 0x1000, 0x1000)),
+             ("sq_graph_launch", lambda: sq.sq_graph_launch(0x1000))]
+    for name, call in calls:
+        sq.sq_debug_fail_next(name)
+        with pytest.raises(sq.SquaresError) as e:
+            call()
+        assert e.value.status == sq.SQ_ECUDA and "injected" in e.value.message, name
+    # one-shot: the next bad-argument call reports its own error again
+    sq.sq_debug_fail_next("sq_u32")
+    sq.sq_debug_fail_next(None)
+    with pytest.raises(sq.SquaresError) as e:
+        sq.sq_u32(1, 0, 10, 0)
+    assert e.value.status == sq.SQ_EINVAL

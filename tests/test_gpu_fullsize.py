@@ -1,6 +1,7 @@
 """Full-size parity: every output of the benchmark workloads, generated in the
-launch configuration the benchmark uses, compared with the oracle chunk by
-chunk on the host (the oracle runs on all host cores).
+launch configuration the benchmark uses (the same autotuning calls first),
+compared with the oracle chunk by chunk on the host (the oracle runs on all
+host cores).
 
   squares64, 2^30 outputs, and squares32, 2^32 outputs, one key (seed 2),
   counter base uniform in [0, 2^64);
@@ -43,6 +44,7 @@ def test_u64_2p30_all_outputs(gpu_lib):
     key = int(gpu_lib.make_keys(2, 1)[0])
     base = workloads.throughput_base(3)
     n = 1 << 30
+    C.sq_autotune(C.SQ_KERNEL_U64, n)  # as bench.py does
     out = torch.empty(n, dtype=torch.int64, device="cuda")
     C.sq_u64(key, base, n, out.data_ptr(), stream_handle())
     _compare_chunks(out, n, lambda a, m: oracle.fill64(key, (base + a) % (1 << 64), m), np.uint64)
@@ -56,6 +58,7 @@ def test_u32_2p32_all_outputs(gpu_lib):
     key = int(gpu_lib.make_keys(2, 1)[0])
     base = workloads.throughput_base(3)
     n = 1 << 32
+    C.sq_autotune(C.SQ_KERNEL_U32, n)  # as bench.py does
     out = torch.empty(n, dtype=torch.int32, device="cuda")
     C.sq_u32(key, base, n, out.data_ptr(), stream_handle())
     _compare_chunks(out, n, lambda a, m: oracle.fill32(key, (base + a) % (1 << 64), m), np.uint32)
@@ -77,6 +80,9 @@ def test_batched_4096_all_outputs(gpu_lib):
     # keep the device inputs referenced until the kernel has run
     d_keys, d_bases = to_dev(keys_dev), to_dev(b.bases)
     d_lengths, d_offsets = to_dev(b.lengths), to_dev(b.offsets)
+    C.sq_autotune_batch(d_keys.data_ptr(), d_bases.data_ptr(), d_lengths.data_ptr(),
+                        d_offsets.data_ptr(), b.nstreams, out.data_ptr())  # as bench.py does
+    out.fill_(0)
     C.sq_batch(d_keys.data_ptr(), d_bases.data_ptr(), d_lengths.data_ptr(), d_offsets.data_ptr(),
                b.nstreams, out.data_ptr(), stream_handle())
 
@@ -104,6 +110,8 @@ def test_transforms_2p30(gpu_lib):
 
     key = int(gpu_lib.make_keys(11, 1)[0])
     n = 1 << 30
+    for kid in (C.SQ_KERNEL_UNIFORM_F32, C.SQ_KERNEL_NORMAL_F32, C.SQ_KERNEL_UNIFORM_BF16):
+        C.sq_autotune(kid, n)  # as bench.py does
     out = torch.empty(n, dtype=torch.int32, device="cuda")
     C.sq_uniform_f32(key, 0, n, out.data_ptr(), stream_handle())
     _compare_chunks(out, n, lambda a, m: oracle.uniform_f32(key, a, m).view(np.uint32), np.uint32)
