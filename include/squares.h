@@ -230,7 +230,9 @@ int sq_autotune_batch(const uint64_t *keys, const uint64_t *ctr_bases, const int
                       const int64_t *offsets, size_t nstreams, uint32_t *out);
 
 /* Persist / restore the tuned table as a small text file keyed by the
- * device name. Loading entries for another device name is a no-op. */
+ * device name. Loading entries for another device name is a no-op. If the
+ * environment variable SQ_TUNE_FILE names such a file, it is loaded on the
+ * library's first use of the table. */
 int sq_autotune_save(const char *path);
 int sq_autotune_load(const char *path);
 

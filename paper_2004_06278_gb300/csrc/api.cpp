@@ -8,8 +8,11 @@
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -114,9 +117,73 @@ struct ConfigTable {
     }
 };
 
-ConfigTable &table() {
+std::string device_name() {
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess)
+        return prop.name;
+    cudaGetLastError();
+    return "unknown";
+}
+
+ConfigTable &raw_table() {
     static ConfigTable t;
     return t;
+}
+
+// Reads a table written by sq_autotune_save into the configuration table.
+// Entries tuned for another device name are ignored (SQ_OK).
+int load_table_file(const char *path, std::string *err) {
+    FILE *f = fopen(path, "r");
+    if (!f) {
+        *err = std::string("cannot open ") + path;
+        return SQ_EINVAL;
+    }
+    char line[512];
+    int version = 0;
+    if (!fgets(line, sizeof line, f) || sscanf(line, "squares-autotune %d", &version) != 1 || version != 1) {
+        fclose(f);
+        *err = std::string(path) + " is not an autotune file";
+        return SQ_EINVAL;
+    }
+    std::string file_dev;
+    if (fgets(line, sizeof line, f) && strncmp(line, "device ", 7) == 0) {
+        file_dev = line + 7;
+        while (!file_dev.empty() && (file_dev.back() == '\n' || file_dev.back() == '\r')) file_dev.pop_back();
+    }
+    if (file_dev != device_name()) {
+        fclose(f);
+        return SQ_OK;  // tuned for another device: keep the defaults
+    }
+    int k, b, v, bl, c;
+    std::vector<std::pair<std::pair<int, int>, sq::Cfg>> rows;
+    while (fgets(line, sizeof line, f)) {
+        if (sscanf(line, "%d %d %d %d %d", &k, &b, &v, &bl, &c) != 5) continue;
+        const sq::Cfg cfg{v, bl, c};
+        if (!valid_kernel(k) || b < 0 || b >= kBuckets || !valid_cfg(k, cfg)) {
+            fclose(f);
+            *err = std::string("bad entry '") + line + "'";
+            return SQ_EINVAL;
+        }
+        rows.push_back({{k, b}, cfg});
+    }
+    fclose(f);
+    ConfigTable &t = raw_table();
+    std::lock_guard<std::mutex> g(t.m);
+    for (auto &r : rows) t.cfg[r.first.first][r.first.second] = r.second;
+    return SQ_OK;
+}
+
+// The configuration table; on first use it is filled from the file named by
+// the environment variable SQ_TUNE_FILE, if that is set and readable.
+ConfigTable &table() {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const char *path = getenv("SQ_TUNE_FILE");
+        std::string err;
+        if (path && *path) load_table_file(path, &err);
+    });
+    return raw_table();
 }
 
 int plain_entry(int kid, uint64_t key, uint64_t base, size_t n, void *out, size_t elem,
@@ -159,6 +226,28 @@ int current_sm_count() {
         sms = 1;
     cache[slot].store(sms, std::memory_order_relaxed);
     return sms;
+}
+
+int occupancy(const void *kernel, int block, size_t smem) {
+    static std::mutex m;
+    static std::map<std::tuple<int, const void *, int, size_t>, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    const auto k = std::make_tuple(dev, kernel, block, smem);
+    {
+        std::lock_guard<std::mutex> g(m);
+        const auto it = cache.find(k);
+        if (it != cache.end()) return it->second;
+    }
+    int blocks = 0;
+    if (!kernel || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, block, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;  // not cached: the query may succeed later
+    }
+    if (blocks < 1) blocks = 1;
+    std::lock_guard<std::mutex> g(m);
+    cache[k] = blocks;
+    return blocks;
 }
 
 }  // namespace sq
@@ -542,11 +631,7 @@ int sq_autotune_batch(const uint64_t *keys, const uint64_t *ctr_bases, const int
 
 int sq_autotune_save(const char *path) {
     if (!path) return fail(SQ_EINVAL, "sq_autotune_save: path is NULL");
-    int dev = 0;
-    cudaDeviceProp prop;
-    std::string name = "unknown";
-    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess)
-        name = prop.name;
+    const std::string name = device_name();
     FILE *f = fopen(path, "w");
     if (!f) return fail(SQ_EINVAL, "sq_autotune_save: cannot open %s", path);
     fprintf(f, "squares-autotune 1\ndevice %s\n", name.c_str());
@@ -565,43 +650,9 @@ int sq_autotune_save(const char *path) {
 
 int sq_autotune_load(const char *path) {
     if (!path) return fail(SQ_EINVAL, "sq_autotune_load: path is NULL");
-    FILE *f = fopen(path, "r");
-    if (!f) return fail(SQ_EINVAL, "sq_autotune_load: cannot open %s", path);
-    char line[512];
-    int version = 0;
-    if (!fgets(line, sizeof line, f) || sscanf(line, "squares-autotune %d", &version) != 1 || version != 1) {
-        fclose(f);
-        return fail(SQ_EINVAL, "sq_autotune_load: %s is not an autotune file", path);
-    }
-    std::string file_dev;
-    if (fgets(line, sizeof line, f) && strncmp(line, "device ", 7) == 0) {
-        file_dev = line + 7;
-        while (!file_dev.empty() && (file_dev.back() == '\n' || file_dev.back() == '\r')) file_dev.pop_back();
-    }
-    int dev = 0;
-    cudaDeviceProp prop;
-    std::string name = "unknown";
-    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess)
-        name = prop.name;
-    if (file_dev != name) {
-        fclose(f);
-        return ok();  // tuned for another device: keep the defaults
-    }
-    int k, b, v, bl, c;
-    std::vector<std::pair<std::pair<int, int>, sq::Cfg>> rows;
-    while (fgets(line, sizeof line, f)) {
-        if (sscanf(line, "%d %d %d %d %d", &k, &b, &v, &bl, &c) != 5) continue;
-        const sq::Cfg cfg{v, bl, c};
-        if (!valid_kernel(k) || b < 0 || b >= kBuckets || !valid_cfg(k, cfg)) {
-            fclose(f);
-            return fail(SQ_EINVAL, "sq_autotune_load: bad entry '%s'", line);
-        }
-        rows.push_back({{k, b}, cfg});
-    }
-    fclose(f);
-    ConfigTable &t = table();
-    std::lock_guard<std::mutex> g(t.m);
-    for (auto &r : rows) t.cfg[r.first.first][r.first.second] = r.second;
+    std::string err;
+    const int rc = load_table_file(path, &err);
+    if (rc != SQ_OK) return fail(rc, "sq_autotune_load: %s", err.c_str());
     return ok();
 }
 

@@ -20,6 +20,11 @@ struct Cfg {
 // Streaming multiprocessors of the current device (cached per device).
 int current_sm_count();
 
+// Resident CTAs per SM for a kernel, block size and dynamic shared memory on
+// the current device (cudaOccupancyMaxActiveBlocksPerMultiprocessor, cached;
+// at least 1).
+int occupancy(const void *kernel, int block, size_t smem);
+
 // --- plain generators (sq_u32, sq_u64, uniform, bf16, normal) -------------
 // kernel_id is one of SQ_KERNEL_U32, _U64, _UNIFORM_F32, _UNIFORM_BF16,
 // _NORMAL_F32, _UNIFORM2_F32, _UNIFORM_F64. `out` is the caller's buffer; element type per kernel.

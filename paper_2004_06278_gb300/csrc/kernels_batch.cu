@@ -221,13 +221,7 @@ const char *batch_variant_name(int variant) {
     return (variant >= 0 && variant < kBatchVariants) ? kBatchVariantNames[variant] : nullptr;
 }
 
-int batch_max_ctas_per_sm(int variant, int block) {
-    int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batch_fn(variant), block, 0) !=
-        cudaSuccess)
-        return 1;
-    return blocks > 0 ? blocks : 1;
-}
+int batch_max_ctas_per_sm(int variant, int block) { return occupancy(batch_fn(variant), block, 0); }
 
 cudaError_t launch_batch(const Cfg &cfg, const uint64_t *keys, const uint64_t *bases,
                          const int64_t *lengths, const int64_t *offsets, size_t nstreams,

@@ -118,11 +118,8 @@ const char *fused_variant_name(int variant) { return variant == 0 ? "warp-item" 
 
 int fused_max_ctas_per_sm(int variant, int block) {
     (void)variant;
-    int blocks = 0;
     const size_t smem = static_cast<size_t>(block / 32) * 256 * sizeof(uint32_t);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fused_kernel, block, smem) != cudaSuccess)
-        return 1;
-    return blocks > 0 ? blocks : 1;
+    return occupancy(reinterpret_cast<const void *>(&fused_kernel), block, smem);
 }
 
 cudaError_t launch_fused(const Cfg &cfg, const uint64_t *keys, const uint64_t *bases,

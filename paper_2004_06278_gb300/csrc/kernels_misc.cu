@@ -48,9 +48,7 @@ __global__ void __launch_bounds__(256)
 }
 
 unsigned grid_for(uint64_t n, const void *fn) {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0) != cudaSuccess || per_sm < 1)
-        per_sm = 1;
+    const int per_sm = occupancy(fn, 256, 0);
     const uint64_t full = static_cast<uint64_t>(current_sm_count()) * per_sm;
     const uint64_t need = (n + 255) / 256;
     return static_cast<unsigned>(need < full ? (need > 0 ? need : 1) : full);

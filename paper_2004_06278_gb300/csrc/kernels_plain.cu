@@ -330,11 +330,7 @@ const void *plain_fn_for(int kernel_id, int variant) {
 
 template <class Op>
 int plain_max_ctas_per_sm_op(int variant, int block) {
-    int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, plain_fn<Op>(variant), block, 0) !=
-        cudaSuccess)
-        return 1;
-    return blocks > 0 ? blocks : 1;
+    return occupancy(plain_fn<Op>(variant), block, 0);
 }
 
 template <class Op>
@@ -414,16 +410,14 @@ const char *plain_variant_name(int variant) {
 
 int plain_max_ctas_per_sm(int kernel_id, int variant, int block) {
     const void *fn = plain_fn_for(kernel_id, variant);
-    int blocks = 0;
+    if (!fn) return 1;
     const size_t smem = variant == kBulkVariant ? bulk_smem(block) : 0;
     if (variant == kBulkVariant) {
         // the opt-in must precede the occupancy query for > 48 KiB
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(bulk_smem(512)));
     }
-    if (!fn || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, block, smem) != cudaSuccess)
-        return 1;
-    return blocks > 0 ? blocks : 1;
+    return occupancy(fn, block, smem);
 }
 
 cudaError_t launch_plain(int kernel_id, const Cfg &cfg, uint64_t key, uint64_t ctr_base, size_t n,

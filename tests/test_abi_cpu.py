@@ -177,3 +177,26 @@ def test_injected_launch_failure_reaches_the_caller(lib):
     with pytest.raises(sq.SquaresError) as e:
         sq.sq_u32(1, 0, 10, 0)
     assert e.value.status == sq.SQ_EINVAL
+
+
+def test_tune_file_from_environment(lib, tmp_path):
+    """SQ_TUNE_FILE: the table is loaded from that file on first use (checked
+    in a fresh process; entries for another device name are ignored)."""
+    import subprocess
+    import sys
+
+    import torch
+
+    name = torch.cuda.get_device_name(0) if torch.cuda.is_available() else "unknown"
+    good = tmp_path / "tune.txt"
+    good.write_text(f"squares-autotune 1\ndevice {name}\n0 20 4 512 2\n")
+    other = tmp_path / "other.txt"
+    other.write_text("squares-autotune 1\ndevice some other GPU\n0 20 4 512 2\n")
+    code = ("import paper_2004_06278_gb300 as sq; c = sq.sq_get_config(0, 1 << 20); "
+            "print(c.variant, c.block, c.ctas_per_sm)")
+    for path, want in ((good, "4 512 2"), (other, "0 256 0")):
+        env = dict(os.environ, SQ_TUNE_FILE=str(path))
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT,
+                           env=env, timeout=120)
+        assert r.returncode == 0, r.stderr
+        assert r.stdout.strip() == want, (path, r.stdout)
