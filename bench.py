@@ -433,9 +433,12 @@ def e2e_block(torch, C, key, base64, base32, dev, steps):
               so copies overlap generation;
       direct: the kernels store straight into the pinned host buffers (the
               buffers are mapped into the device's address space; on GB300
-              the stores cross NVLink-C2C).
+              the stores cross NVLink-C2C). For host-resident outputs the
+              library uses the contiguous 32-byte-per-lane stores whatever
+              variant is tuned for device memory.
     The step's inputs are two 64-bit scalars passed by value in the launch
-    (no host-to-device copy)."""
+    (no host-to-device copy). `link_GBps` is a plain device-to-host copy of
+    one staging buffer, the ceiling of either path."""
     chunk = 1 << 28  # elements
     host64 = torch.empty(N64, dtype=torch.int64, pin_memory=True)
     host32 = torch.empty(N32, dtype=torch.int32, pin_memory=True)
@@ -471,13 +474,20 @@ def e2e_block(torch, C, key, base64, base32, dev, steps):
             fn()
         return (time.perf_counter() - t0) / steps
 
+    def run_link():
+        with torch.cuda.stream(streams[0]):
+            host64.view(torch.uint8)[:chunk * 8].copy_(stage[0], non_blocking=True)
+        streams[0].synchronize()
+
     dt_copy = timed(run_copy)
     dt_direct = timed(run_direct)
+    dt_link = timed(run_link)
     d2h = 8 * N64 + 4 * N32
     best = min(dt_copy, dt_direct)
     res = {"value": (N64 + N32) / best / 1e9, "unit": "Gsamples/s", "h2d_bytes_per_step": 0,
            "d2h_bytes_per_step": d2h, "ms_per_step": best * 1000, "steps": steps,
-           "d2h_GBps": d2h / best / 1e9,
+           "d2h_GBps": d2h / best / 1e9, "link_GBps": chunk * 8 / dt_link / 1e9,
+           "frac_of_link": (d2h / best) / (chunk * 8 / dt_link),
            "path": "direct: kernels store into pinned host memory" if dt_direct <= dt_copy else
                    "copy: 2 GiB device chunks, cudaMemcpyAsync to pinned host, 2 streams",
            "copy_ms_per_step": dt_copy * 1000, "direct_ms_per_step": dt_direct * 1000}

@@ -214,6 +214,15 @@ int batch_checks(const uint64_t *keys, const uint64_t *bases, const int64_t *len
 
 namespace sq {
 
+bool in_device_memory(const void *p) {
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice;
+}
+
 int current_sm_count() {
     static std::array<std::atomic<int>, 64> cache{};
     int dev = 0;

@@ -25,6 +25,10 @@ int current_sm_count();
 // at least 1).
 int occupancy(const void *kernel, int block, size_t smem);
 
+// True when `p` is device memory of the current context. Pinned, registered
+// or plain system host memory (written over the host link) gives false.
+bool in_device_memory(const void *p);
+
 // --- plain generators (sq_u32, sq_u64, uniform, bf16, normal) -------------
 // kernel_id is one of SQ_KERNEL_U32, _U64, _UNIFORM_F32, _UNIFORM_BF16,
 // _NORMAL_F32, _UNIFORM2_F32, _UNIFORM_F64. `out` is the caller's buffer; element type per kernel.

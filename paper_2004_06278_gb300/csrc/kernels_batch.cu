@@ -227,12 +227,15 @@ cudaError_t launch_batch(const Cfg &cfg, const uint64_t *keys, const uint64_t *b
                          const int64_t *lengths, const int64_t *offsets, size_t nstreams,
                          uint32_t *out, cudaStream_t stream) {
     if (nstreams == 0) return cudaSuccess;
-    const int ctas = cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : batch_max_ctas_per_sm(cfg.variant, cfg.block);
+    Cfg c = cfg;
+    // Host-resident outputs: contiguous 1 KiB warp stores (see launch_plain).
+    if (c.variant >= 2 && !in_device_memory(out)) c.variant -= 2;
+    const int ctas = c.ctas_per_sm > 0 ? c.ctas_per_sm : batch_max_ctas_per_sm(c.variant, c.block);
     const unsigned grid = static_cast<unsigned>(current_sm_count()) * static_cast<unsigned>(ctas);
     const uintptr_t addr = reinterpret_cast<uintptr_t>(out);
     const uint32_t head = static_cast<uint32_t>(((32 - (addr % 32)) % 32) / 4);
     const uint32_t S = static_cast<uint32_t>(nstreams);
-    switch (cfg.variant) {
+    switch (c.variant) {
         case 0: batch_kernel<false, 8><<<grid, cfg.block, 0, stream>>>(keys, bases, lengths, offsets, S, out, head); break;
         case 1: batch_kernel<true, 8><<<grid, cfg.block, 0, stream>>>(keys, bases, lengths, offsets, S, out, head); break;
         case 2: batch_kernel<false, 16><<<grid, cfg.block, 0, stream>>>(keys, bases, lengths, offsets, S, out, head); break;

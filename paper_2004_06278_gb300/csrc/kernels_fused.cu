@@ -1,14 +1,17 @@
 // Generation-only statistics: squares32 values are consumed in registers.
 //
 // Work is split into items (stream s, part p); one warp takes an item and
-// each lane walks a contiguous run of its counters by Weyl addition. A lane
-// keeps its XOR and top-byte sum in registers; the warp combines them with
-// shuffles and lane 0 merges them into the stream's outputs with one atomic
-// each (the outputs were cleared on the stream beforehand, so the result
-// does not depend on how streams are split into parts). The top-byte
-// histogram is kept per warp in shared memory and flushed to the global
-// 256-bin histogram at the end, or earlier if a warp's 32-bit bins could
-// overflow. Nothing but the statistics is written to global memory.
+// each lane walks a contiguous run of its counters by Weyl addition. The
+// top-byte histogram is kept per warp in shared memory and flushed to the
+// global 256-bin histogram at the end, or earlier if a warp's 32-bit bins
+// could overflow. A lane keeps only its XOR in registers. The item's
+// top-byte sum is read off the warp's histogram: sum over bins of b * h[b]
+// grows by exactly that sum while the warp walks the item, so per value the
+// loop pays for the histogram increment alone. The warp combines the XORs
+// with shuffles and lane 0 merges XOR and sum into the stream's outputs with
+// one atomic each (the outputs were cleared on the stream beforehand, so
+// the result does not depend on how streams are split into parts). Nothing
+// but the statistics is written to global memory.
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -32,6 +35,18 @@ __device__ __forceinline__ void flush_hist(uint32_t *h, uint64_t *__restrict__ h
     __syncwarp();
 }
 
+// Sum over the warp's bins of b * h[b], in every lane. Bins hold < 2^32
+// each (flushes come every 2^31 counters at most), so 64 bits are exact.
+__device__ __forceinline__ uint64_t weighted_bins(const uint32_t *h, int lane) {
+    __syncwarp();
+    uint64_t w = 0;
+#pragma unroll
+    for (int b = lane; b < 256; b += 32) w += static_cast<uint64_t>(h[b]) * static_cast<uint32_t>(b);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xFFFFFFFFu, w, o);
+    return w;
+}
+
 __global__ void __launch_bounds__(512)
     fused_kernel(const uint64_t *__restrict__ keys, const uint64_t *__restrict__ bases, uint64_t S,
                  uint64_t C, uint64_t parts, uint64_t part_len, uint32_t *__restrict__ xor_out,
@@ -46,6 +61,7 @@ __global__ void __launch_bounds__(512)
     const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
     const uint64_t items = S * parts;
     uint64_t since_flush = 0;
+    uint64_t weighted = 0;  // weighted_bins(h) as of the last item's end
     for (uint64_t w = gwarp; w < items; w += nwarps) {
         const uint64_t s = w / parts;
         const uint64_t a = (w - s * parts) * part_len;
@@ -58,7 +74,7 @@ __global__ void __launch_bounds__(512)
         uint64_t t = round1_value(y);  // round 1 by the recurrence of round1_delta
         uint64_t er = round1_delta(y, key);
         const uint64_t c2 = (key * key) << 1;
-        uint32_t x = 0, sum = 0;
+        uint32_t x = 0;
         const uint64_t cnt = (lb > la) ? lb - la : 0;
         // Blocks of 8 counters: t_{j+1} = t_j + e + j*c2 with e fixed for the
         // block (one three-input addition per value), e += 8*c2 per block.
@@ -75,7 +91,6 @@ __global__ void __launch_bounds__(512)
                 y = yn;
                 t = add64x3(t, er, jc2[j]);
                 x ^= u;
-                sum += u >> 24;
                 atomicAdd(h + (u >> 24), 1u);
             }
             er = add64(er, c2x8);
@@ -87,24 +102,22 @@ __global__ void __launch_bounds__(512)
             t = add64(t, er);
             er = add64(er, c2);
             x ^= u;
-            sum += u >> 24;
             atomicAdd(h + (u >> 24), 1u);
         }
-        uint64_t sum64 = sum;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            x ^= __shfl_xor_sync(0xFFFFFFFFu, x, o);
-            sum64 += __shfl_xor_sync(0xFFFFFFFFu, sum64, o);
-        }
+        for (int o = 16; o > 0; o >>= 1) x ^= __shfl_xor_sync(0xFFFFFFFFu, x, o);
+        const uint64_t now = weighted_bins(h, lane);
         if (lane == 0) {
             atomicXor(xor_out + s, x);
             atomicAdd(reinterpret_cast<unsigned long long *>(sum_top + s),
-                      static_cast<unsigned long long>(sum64));
+                      static_cast<unsigned long long>(now - weighted));
         }
+        weighted = now;
         since_flush += b - a;
         if (since_flush >= kFlushEvery) {
             flush_hist(h, hist, lane);
             since_flush = 0;
+            weighted = 0;
         }
     }
     flush_hist(h, hist, lane);
@@ -137,8 +150,8 @@ cudaError_t launch_fused(const Cfg &cfg, const uint64_t *keys, const uint64_t *b
     const int ctas = cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : fused_max_ctas_per_sm(0, cfg.block);
     const uint64_t grid = static_cast<uint64_t>(current_sm_count()) * ctas;
     const uint64_t warps = grid * (cfg.block / 32);
-    // Parts per stream: each item at most 2^29 counters (so a lane's 32-bit
-    // top-byte sum cannot overflow), and at least ~4 items per warp when
+    // Parts per stream: each item at most 2^29 counters (so a warp's 32-bit
+    // bins stay below 2^32 between flushes), and at least ~4 items per warp when
     // there are few streams, but never parts shorter than 1024 counters.
     uint64_t parts = (ctrs_per_stream + (1ull << 29) - 1) >> 29;
     const uint64_t want = (4 * warps + nstreams - 1) / nstreams;

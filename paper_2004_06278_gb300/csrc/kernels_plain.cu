@@ -329,11 +329,6 @@ const void *plain_fn_for(int kernel_id, int variant) {
 }
 
 template <class Op>
-int plain_max_ctas_per_sm_op(int variant, int block) {
-    return occupancy(plain_fn<Op>(variant), block, 0);
-}
-
-template <class Op>
 cudaError_t launch_bulk(const Cfg &cfg, uint64_t key, uint64_t ctr0, size_t n, void *out,
                         cudaStream_t stream, int max_ctas) {
     using T = typename Op::T;
@@ -361,18 +356,7 @@ template <class Op>
 cudaError_t launch_op(const Cfg &cfg, uint64_t key, uint64_t ctr0, size_t n, void *out,
                       cudaStream_t stream, int max_ctas) {
     using T = typename Op::T;
-    if (cfg.variant == kBulkVariant) {
-        // The copy engine path is used for device memory only; anything else
-        // (pinned or managed host memory) takes the direct 64-byte stores.
-        cudaPointerAttributes attr;
-        if (cudaPointerGetAttributes(&attr, out) == cudaSuccess && attr.type == cudaMemoryTypeDevice)
-            return launch_bulk<Op>(cfg, key, ctr0, n, out, stream, max_ctas);
-        cudaGetLastError();
-        Cfg direct = cfg;
-        direct.variant = 4;
-        const int mc = cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : plain_max_ctas_per_sm_op<Op>(4, cfg.block);
-        return launch_op<Op>(direct, key, ctr0, n, out, stream, mc);
-    }
+    if (cfg.variant == kBulkVariant) return launch_bulk<Op>(cfg, key, ctr0, n, out, stream, max_ctas);
     const int bytes = variant_bytes(cfg.variant);
     const int align = bytes > 32 ? 32 : bytes;  // each store is at most 32 B
     const size_t epv = bytes / sizeof(T);
@@ -423,21 +407,28 @@ int plain_max_ctas_per_sm(int kernel_id, int variant, int block) {
 cudaError_t launch_plain(int kernel_id, const Cfg &cfg, uint64_t key, uint64_t ctr_base, size_t n,
                          void *out, cudaStream_t stream) {
     if (n == 0) return cudaSuccess;
-    const int max_ctas = cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm
-                                             : plain_max_ctas_per_sm(kernel_id, cfg.variant, cfg.block);
+    Cfg c = cfg;
+    // Outputs outside device memory (pinned or system host memory, written
+    // over the host link) take the 32-byte-per-lane stores, where one warp
+    // store fills a contiguous 1 KiB. The 64-byte-per-lane forms leave each
+    // 128 B line half written per store, which halves the link's write rate,
+    // and the bulk copy stages for device memory only.
+    if (variant_bytes(c.variant) > 32 && !in_device_memory(out)) c.variant = c.variant == 5 ? 1 : 0;
+    const int max_ctas = c.ctas_per_sm > 0 ? c.ctas_per_sm
+                                           : plain_max_ctas_per_sm(kernel_id, c.variant, c.block);
     switch (kernel_id) {
-        case SQ_KERNEL_U32: return launch_op<OpU32>(cfg, key, ctr_base, n, out, stream, max_ctas);
-        case SQ_KERNEL_U64: return launch_op<OpU64>(cfg, key, ctr_base, n, out, stream, max_ctas);
+        case SQ_KERNEL_U32: return launch_op<OpU32>(c, key, ctr_base, n, out, stream, max_ctas);
+        case SQ_KERNEL_U64: return launch_op<OpU64>(c, key, ctr_base, n, out, stream, max_ctas);
         case SQ_KERNEL_UNIFORM_F32:
-            return launch_op<OpUniformF32>(cfg, key, ctr_base, n, out, stream, max_ctas);
+            return launch_op<OpUniformF32>(c, key, ctr_base, n, out, stream, max_ctas);
         case SQ_KERNEL_UNIFORM_BF16:
-            return launch_op<OpUniformBF16>(cfg, key, ctr_base, n, out, stream, max_ctas);
+            return launch_op<OpUniformBF16>(c, key, ctr_base, n, out, stream, max_ctas);
         case SQ_KERNEL_NORMAL_F32:
-            return launch_op<OpNormalF32>(cfg, key, ctr_base, n, out, stream, max_ctas);
+            return launch_op<OpNormalF32>(c, key, ctr_base, n, out, stream, max_ctas);
         case SQ_KERNEL_UNIFORM2_F32:
-            return launch_op<OpUniform2F32>(cfg, key, ctr_base, n, out, stream, max_ctas);
+            return launch_op<OpUniform2F32>(c, key, ctr_base, n, out, stream, max_ctas);
         case SQ_KERNEL_UNIFORM_F64:
-            return launch_op<OpUniformF64>(cfg, key, ctr_base, n, out, stream, max_ctas);
+            return launch_op<OpUniformF64>(c, key, ctr_base, n, out, stream, max_ctas);
         default: return cudaErrorInvalidValue;
     }
 }

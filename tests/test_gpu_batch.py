@@ -154,3 +154,53 @@ def test_validate(gpu_lib):
     offsets.copy_(to_dev(b.offsets))
     with pytest.raises(C.SquaresError):
         C.sq_batch_validate(lengths.data_ptr(), offsets.data_ptr(), b.nstreams, stream_handle())
+
+
+def test_every_variant_into_pinned_host_memory(gpu_lib):
+    """A batch written to pinned host memory (the wide variants are replaced
+    by contiguous stores there) matches the oracle, canaries intact."""
+    import torch
+
+    b = workloads.small_ragged_batch(150, seed=43, max_len=30_000)
+    keys, bases, lengths, offsets = _device_inputs(gpu_lib, b)
+    n_out = b.total + 19
+    want = _expect(b, n_out)
+    host = torch.empty(n_out + 8, dtype=torch.int32, pin_memory=True)
+    try:
+        for v in range(C.sq_num_variants(C.SQ_KERNEL_BATCH)):
+            C.sq_set_config(C.SQ_KERNEL_BATCH, 0, v, 256, 0)
+            for off in (0, 5):
+                host.numpy().view(np.uint32)[:] = FILL
+                C.sq_batch(keys.data_ptr(), bases.data_ptr(), lengths.data_ptr(), offsets.data_ptr(),
+                           b.nstreams, host[off:].data_ptr(), stream_handle())
+                torch.cuda.synchronize()
+                got = host.numpy().view(np.uint32)
+                assert np.array_equal(got[off:off + n_out], want), (v, off)
+                assert np.all(got[:off] == FILL) and np.all(got[off + n_out:] == FILL), (v, off)
+    finally:
+        C.sq_set_config(C.SQ_KERNEL_BATCH, 0, 0, 256, 0)
+
+
+def test_capture_with_wide_variant(gpu_lib):
+    """The output-memory query made for the wide variants is legal inside a
+    stream capture: capture with the widest variant and replay."""
+    import torch
+
+    b = workloads.small_ragged_batch(60, seed=47, max_len=20_000)
+    keys, bases, lengths, offsets = _device_inputs(gpu_lib, b)
+    n_out = b.total + 7
+    out = filled_u32(n_out, int(FILL))
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    try:
+        C.sq_set_config(C.SQ_KERNEL_BATCH, 0, C.sq_num_variants(C.SQ_KERNEL_BATCH) - 1, 256, 0)
+        with torch.cuda.stream(s):
+            gpu_lib.batch(keys, bases, lengths, offsets, out)
+            s.synchronize()
+            with torch.cuda.graph(g, stream=s):
+                gpu_lib.batch(keys, bases, lengths, offsets, out)
+        out.copy_(filled_u32(n_out, int(FILL)))
+        g.replay()
+        assert np.array_equal(host_u32(out), _expect(b, n_out))
+    finally:
+        C.sq_set_config(C.SQ_KERNEL_BATCH, 0, 0, 256, 0)

@@ -146,3 +146,29 @@ def test_bulk_variant_device_and_host_memory(gpu_lib):
     finally:
         C.sq_set_config(C.SQ_KERNEL_U32, 0, 0, 256, 0)
         C.sq_set_config(C.SQ_KERNEL_U64, 0, 0, 256, 0)
+
+
+@pytest.mark.parametrize("kid,fn,dt,ref", [(C.SQ_KERNEL_U32, C.sq_u32, "int32", oracle.fill32),
+                                           (C.SQ_KERNEL_U64, C.sq_u64, "int64", oracle.fill64)])
+def test_every_variant_into_pinned_host_memory(gpu_lib, kid, fn, dt, ref):
+    """Outputs in pinned host memory: each configured variant (the wide and
+    bulk ones are replaced by contiguous stores there) gives the oracle's
+    bits, at an aligned and a misaligned start."""
+    import torch
+
+    key = int(gpu_lib.make_keys(12, 1)[0])
+    n = 2 * 152 * 512 * 16 + 29
+    want = ref(key, M64 - 5, n)
+    host = torch.zeros(n + 8, dtype=getattr(torch, dt), pin_memory=True)
+    try:
+        for v in range(C.sq_num_variants(kid)):
+            C.sq_set_config(kid, 0, v, 256, 0)
+            for off in (0, 3):
+                host.zero_()
+                fn(key, M64 - 5, n, host[off:].data_ptr(), stream_handle())
+                torch.cuda.synchronize()
+                got = host.numpy().view(want.dtype)
+                assert np.array_equal(got[off:off + n], want), (v, off)
+                assert not got[:off].any() and not got[off + n:].any(), (v, off)
+    finally:
+        C.sq_set_config(kid, 0, 0, 256, 0)
