@@ -16,6 +16,7 @@ Every function names the paper passage it follows:
   uniform_f32 / uniform_bf16 ..... float conversion (Section 5 prose), FP64
   uniform2_f32 / uniform_f64 ..... two floats / one 53-bit double per squares64
   normal_f64 ..................... Box-Muller on squares64 halves, FP64
+  box_muller_f64 ................. the same pair for given 32-bit halves
   fused_stats .................... XOR / top-byte sum / top-byte histogram
   make_keys ...................... "different digits" keys (Section 3)
   squares_w / hist_w ............. reduced-width analogue for brute force
@@ -81,6 +82,7 @@ def _load():
             "oracle_uniform_f32": (None, [_u64, _u64, _u64, _p]),
             "oracle_uniform_bf16": (None, [_u64, _u64, _u64, _p]),
             "oracle_normal_f64": (None, [_u64, _u64, _u64, _p]),
+            "oracle_box_muller_f64": (None, [_p, _p, _u64, _p]),
             "oracle_fused_stats": (None, [_p, _p, _u64, _u64, _p, _p, _p]),
             "oracle_make_keys": (_i, [_u64, _u64, _p]),
             "oracle_splitmix64": (None, [_u64, _u64, _p]),
@@ -271,6 +273,24 @@ def normal_f64(key: int, base: int, n: int, threads: int | None = None) -> np.nd
         lib.oracle_normal_f64(key, (base + a) & M64, count, addr + 8 * 2 * a)
 
     _parallel(run, _chunks(npairs, threads), threads)
+    return out
+
+
+def box_muller_f64(hi, lo, threads: int | None = None) -> np.ndarray:
+    """Box-Muller pairs in FP64 for given upper / lower halves: row i is
+    (r cos theta, r sin theta) with u1 = (hi[i] + 1) / 2^32 and
+    theta = 2 pi lo[i] / 2^32."""
+    lib = _load()
+    hi = np.ascontiguousarray(hi, dtype=np.uint32)
+    lo = np.ascontiguousarray(lo, dtype=np.uint32)
+    assert hi.shape == lo.shape and hi.ndim == 1
+    out = np.empty((hi.size, 2), dtype=np.float64)
+    threads = threads or default_threads()
+
+    def run(a, b):
+        lib.oracle_box_muller_f64(_ptr(hi) + 4 * a, _ptr(lo) + 4 * a, b - a, _ptr(out) + 16 * a)
+
+    _parallel(run, _chunks(hi.size, threads), threads)
     return out
 
 

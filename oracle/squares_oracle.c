@@ -230,25 +230,38 @@ void oracle_uniform_f64(uint64_t key, uint64_t base, uint64_t n, double *out) {
     }
 }
 
-/* Standard normals by the Box-Muller transform from squares64 outputs.
- * Output j = squares64(base + j, key) supplies the pair (2j, 2j+1):
- *   hi = upper 32 bits, lo = lower 32 bits,
+/* The Box-Muller pair from the two 32-bit halves of one squares64 output:
  *   u1 = (hi + 1) / 2^32 in (0, 1],  theta = 2 pi lo / 2^32,
- *   r  = sqrt(-2 ln u1),  z[2j] = r cos theta,  z[2j+1] = r sin theta.
- * An odd n drops the last sine. All in double precision. */
-void oracle_normal_f64(uint64_t key, uint64_t base, uint64_t n, double *out) {
+ *   r  = sqrt(-2 ln u1),  z0 = r cos theta,  z1 = r sin theta.
+ * All in double precision. */
+static void box_muller_pair(uint32_t hi, uint32_t lo, double *z0, double *z1) {
     const double two_pi = 6.283185307179586476925286766559;
+    const double u1 = ((double)hi + 1.0) / 4294967296.0;
+    const double theta = two_pi * ((double)lo / 4294967296.0);
+    const double r = sqrt(-2.0 * log(u1));
+    *z0 = r * cos(theta);
+    *z1 = r * sin(theta);
+}
+
+/* Standard normals by the Box-Muller transform from squares64 outputs.
+ * Output j = squares64(base + j, key) supplies the pair (2j, 2j+1) from
+ * hi = its upper 32 bits and lo = its lower 32 bits (box_muller_pair).
+ * An odd n drops the last sine. */
+void oracle_normal_f64(uint64_t key, uint64_t base, uint64_t n, double *out) {
     uint64_t j;
     for (j = 0; 2 * j < n; ++j) {
         const uint64_t v = oracle_squares64(base + j, key);
-        const double hi = (double)(v >> 32);
-        const double lo = (double)(v & 0xffffffffu);
-        const double u1 = (hi + 1.0) / 4294967296.0;
-        const double theta = two_pi * (lo / 4294967296.0);
-        const double r = sqrt(-2.0 * log(u1));
-        out[2 * j] = r * cos(theta);
-        if (2 * j + 1 < n) out[2 * j + 1] = r * sin(theta);
+        double z0, z1;
+        box_muller_pair((uint32_t)(v >> 32), (uint32_t)v, &z0, &z1);
+        out[2 * j] = z0;
+        if (2 * j + 1 < n) out[2 * j + 1] = z1;
     }
+}
+
+/* The same pair for given halves: out[2i], out[2i+1] from (hi[i], lo[i]). */
+void oracle_box_muller_f64(const uint32_t *hi, const uint32_t *lo, uint64_t n, double *out) {
+    uint64_t i;
+    for (i = 0; i < n; ++i) box_muller_pair(hi[i], lo[i], &out[2 * i], &out[2 * i + 1]);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -210,3 +210,37 @@ def run_scalar_battery(sq32, sq64, seed=20040627):
     pin_even_key_period(sq32, sq64, rng)
     pin_odd_key_not_periodic(sq32, sq64, rng)
     pin_z_term(sq32, sq64, rng, n=100)
+
+
+# --- Box-Muller on 32-bit halves --------------------------------------------
+
+def pin_box_muller_closed_forms(bm):
+    """u1 = 1 gives the origin; lo = 0, 2^30, 2^31, 3*2^30 put the pair on
+    the axes; hi = 0 gives the largest radius sqrt(64 ln 2); hi = 2^31 - 1
+    gives u1 = 1/2, radius sqrt(2 ln 2); lo = 2^29 is the diagonal."""
+    M = (1 << 32) - 1
+    hi = np.array([M, M, 0, 0, 0, 0, (1 << 31) - 1, (1 << 31) - 1], dtype=np.uint32)
+    lo = np.array([0, 12345, 0, 1 << 30, 1 << 31, 3 << 30, 1 << 29, 0], dtype=np.uint32)
+    z = bm(hi, lo)
+    rmax, rhalf = np.sqrt(64 * np.log(2)), np.sqrt(2 * np.log(2))
+    want = np.array([[0, 0], [0, 0], [rmax, 0], [0, rmax], [-rmax, 0], [0, -rmax],
+                     [rhalf / np.sqrt(2), rhalf / np.sqrt(2)], [rhalf, 0]])
+    assert np.allclose(z, want, rtol=0, atol=1e-14), z
+
+
+def pin_box_muller_polar(bm, rng, n=5000):
+    """Radius and angle recovered from the pairs of random halves:
+    r^2 = -2 ln((hi + 1) / 2^32), angle = 2 pi lo / 2^32."""
+    hi = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
+    lo = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
+    z = bm(hi, lo)
+    r2 = z[:, 0] ** 2 + z[:, 1] ** 2
+    assert np.allclose(r2, -2 * np.log((hi.astype(np.float64) + 1) / 2 ** 32), rtol=1e-12, atol=1e-12)
+    ang = np.mod(np.arctan2(z[:, 1], z[:, 0]), 2 * np.pi)
+    dang = np.angle(np.exp(1j * (ang - 2 * np.pi * lo.astype(np.float64) / 2 ** 32)))
+    assert np.all(np.abs(dang[r2 > 1e-6]) < 1e-9)
+
+
+def run_box_muller_battery(bm, seed=20040627):
+    pin_box_muller_closed_forms(bm)
+    pin_box_muller_polar(bm, np.random.default_rng(seed))

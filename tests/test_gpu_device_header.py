@@ -40,6 +40,17 @@ __global__ void by_stream(uint64_t key, uint64_t ctr0, uint64_t per, uint64_t st
     }
 }
 
+__global__ void bm_pairs(const uint32_t *hi, const uint32_t *lo, uint64_t n, float2 *out) {
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = sq::box_muller(hi[i], lo[i]);
+}
+
+extern "C" int run_bm_pairs(const uint32_t *hi, const uint32_t *lo, uint64_t n, float2 *out) {
+    bm_pairs<<<(unsigned)((n + 255) / 256), 256>>>(hi, lo, n, out);
+    return (int)cudaDeviceSynchronize();
+}
+
 extern "C" int run_by_counter(uint64_t key, uint64_t ctr0, uint64_t n, uint32_t *o32, uint64_t *o64,
                               double *of64) {
     by_counter<<<(unsigned)((n + 255) / 256), 256>>>(key, ctr0, n, o32, o64, of64);
@@ -66,6 +77,7 @@ def consumer(tmp_path_factory):
     u64, p = ctypes.c_uint64, ctypes.c_void_p
     lib.run_by_counter.argtypes = [u64, u64, u64, p, p, p]
     lib.run_by_stream.argtypes = [u64, u64, u64, u64, u64, p, p]
+    lib.run_bm_pairs.argtypes = [p, p, u64, p]
     return lib
 
 
@@ -97,3 +109,45 @@ def test_weyl_stream(gpu_lib, consumer, step):
     assert consumer.run_by_stream(key, base, per, step, nth, o32.data_ptr(), o64.data_ptr()) == 0
     assert np.array_equal(o32.cpu().numpy().view(np.uint32), oracle.fill32_strided(key, base, step, n))
     assert np.array_equal(o64.cpu().numpy().view(np.uint64), oracle.fill64_strided(key, base, step, n))
+
+
+def _edge_halves(rng):
+    """hi: both ends of the range, every power of two and every switch of
+    the exponent split (2^E sqrt2), each +-64, plus random values; lo:
+    every quadrant boundary (multiples of 2^29) +-64, plus random values."""
+    M = 1 << 32
+    his = [np.arange(0, 1 << 16), np.arange(M - (1 << 16), M)]
+    for e in range(33):
+        for c in (1 << e, int(round((1 << e) * np.sqrt(2)))):
+            his.append(np.arange(c - 65, c + 64))  # k = hi + 1 in [c - 64, c + 64]
+    his.append(rng.integers(0, M, 1 << 20))
+    hi_edge = np.concatenate(his)
+    hi_edge = hi_edge[(hi_edge >= 0) & (hi_edge < M)].astype(np.uint64).astype(np.uint32)
+    lo_edge = np.concatenate([(np.arange(-64, 65) + (j << 29)) % M for j in range(8)]
+                             + [rng.integers(0, M, 1 << 18)]).astype(np.uint64).astype(np.uint32)
+    hi = np.concatenate([hi_edge, rng.integers(0, M, lo_edge.size).astype(np.uint32)])
+    lo = np.concatenate([rng.integers(0, M, hi_edge.size).astype(np.uint32), lo_edge])
+    return hi, lo
+
+
+def test_box_muller_edges(gpu_lib, consumer):
+    """sq::box_muller on the edges of its exponent split and quadrant
+    reduction, against the oracle's double-precision pair: within 2e-6
+    absolute where |z| < 5 and 1e-5 relative beyond."""
+    import torch
+
+    hi, lo = _edge_halves(np.random.default_rng(61))
+    n = hi.size
+    d_hi = torch.from_numpy(hi.view(np.int32)).cuda()
+    d_lo = torch.from_numpy(lo.view(np.int32)).cuda()
+    out = torch.empty((n, 2), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    assert consumer.run_bm_pairs(d_hi.data_ptr(), d_lo.data_ptr(), n, out.data_ptr()) == 0
+    got = out.cpu().numpy().astype(np.float64)
+    want = oracle.box_muller_f64(hi, lo)
+    err = np.abs(got - want)
+    small = np.abs(want) < 5
+    assert err[small].max() <= 2e-6, err[small].max()
+    if (~small).any():
+        assert (err[~small] / np.abs(want[~small])).max() <= 1e-5
+    assert np.all(np.isfinite(got))

@@ -62,14 +62,14 @@ def test_normal_within_bounds(gpu_lib, n):
 
 def test_normal_edge_integers(gpu_lib):
     """Counters whose squares64 outputs have hi near 0 (deep tail), near
-    2^32 - 2^25 (the switch from log to log1p, 1 - u1 = 2^-7) and near
-    2^32 - 1 (u1 -> 1, r -> 0): found by scanning the oracle's outputs, then
-    generated on the GPU."""
+    2^32 / sqrt2 (the last switch of the exponent split, u1 = 1/sqrt2) and
+    near 2^32 - 1 (u1 -> 1, r -> 0): found by scanning the oracle's outputs,
+    then generated on the GPU."""
     key = int(gpu_lib.make_keys(11, 1)[0])
     n_pairs = 1 << 24
     v = oracle.fill64(key, 0, n_pairs)
     hi = v >> np.uint64(32)
-    switch = (1 << 32) - 1 - (1 << 25)
+    switch = int(round((1 << 32) / np.sqrt(2))) - 1
     picks = np.concatenate([np.argsort(hi)[:64], np.argsort(hi)[-64:],
                             np.argsort(np.abs(hi.astype(np.int64) - switch))[:64]])
     for j in picks:

@@ -94,3 +94,53 @@ def test_mutant_is_rejected(tmp_path, name, old, new, occ):
     sq32, sq64 = _build(tmp_path, "mutant", mutated)
     with pytest.raises(AssertionError):
         pins.run_scalar_battery(sq32, sq64)
+
+
+# Planted mistakes in the Box-Muller pair; the battery of closed forms and
+# polar identities must reject each.
+BM_MUTANTS = [
+    ("u1 = (hi + 1/2) / 2^32", "((double)hi + 1.0) / 4294967296.0", "((double)hi + 0.5) / 4294967296.0"),
+    ("radius without the factor 2", "sqrt(-2.0 * log(u1))", "sqrt(-log(u1))"),
+    ("cosine and sine exchanged", "*z0 = r * cos(theta);", "*z0 = r * sin(theta);"),
+    ("angle pi lo / 2^32", "two_pi * ((double)lo", "0.5 * two_pi * ((double)lo"),
+    ("sine negated", "*z1 = r * sin(theta);", "*z1 = -r * sin(theta);"),
+    ("halves exchanged", "((double)hi + 1.0) / 4294967296.0", "((double)lo + 1.0) / 4294967296.0"),
+]
+
+
+def _build_bm(tmp_path, name, text):
+    import numpy as np
+
+    c = tmp_path / f"{name}.c"
+    so = tmp_path / f"{name}.so"
+    c.write_text(text)
+    subprocess.run(["gcc", "-O1", "-std=c99", "-shared", "-fPIC", str(c), "-o", str(so), "-lm"],
+                   check=True)
+    lib = ctypes.CDLL(str(so))
+    p = ctypes.c_void_p
+    lib.oracle_box_muller_f64.argtypes = [p, p, ctypes.c_uint64, p]
+
+    def bm(hi, lo):
+        hi = np.ascontiguousarray(hi, dtype=np.uint32)
+        lo = np.ascontiguousarray(lo, dtype=np.uint32)
+        out = np.empty((hi.size, 2), dtype=np.float64)
+        lib.oracle_box_muller_f64(hi.ctypes.data, lo.ctypes.data, hi.size, out.ctypes.data)
+        return out
+
+    return bm
+
+
+def test_unmutated_box_muller_passes(tmp_path):
+    with open(SRC) as f:
+        src = f.read()
+    pins.run_box_muller_battery(_build_bm(tmp_path, "clean_bm", src))
+
+
+@pytest.mark.parametrize("name,old,new", BM_MUTANTS, ids=[m[0] for m in BM_MUTANTS])
+def test_box_muller_mutant_is_rejected(tmp_path, name, old, new):
+    with open(SRC) as f:
+        src = f.read()
+    mutated = _mutate(src, old, new, 0)
+    assert mutated != src
+    with pytest.raises(AssertionError):
+        pins.run_box_muller_battery(_build_bm(tmp_path, "mutant_bm", mutated))

@@ -77,6 +77,22 @@ def test_normal_polar_form():
     assert np.array_equal(z_odd, z[:7])
 
 
+def test_box_muller_pairs_battery():
+    """The per-halves form against closed-form points and the polar
+    identities (tests/pins.py)."""
+    pins.run_box_muller_battery(oracle.box_muller_f64)
+
+
+def test_box_muller_pairs_match_normals():
+    """On squares64 outputs the per-halves form equals the normals of those
+    counters."""
+    v = oracle.fill64(key(), 21, 5000)
+    hi = (v >> np.uint64(32)).astype(np.uint32)
+    lo = (v & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    z = oracle.box_muller_f64(hi, lo)
+    assert np.array_equal(z.reshape(-1), oracle.normal_f64(key(), 21, 10_000))
+
+
 def test_batch_is_concatenation_and_leaves_gaps():
     rng = np.random.default_rng(3)
     S = 9
