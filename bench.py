@@ -161,16 +161,17 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # reference arm: the oracle on the host cores
 
-def oracle_sample_rate(n64: int, n32: int, chunk: int = 1 << 26):
+def oracle_sample_rate(n64: int, n32: int, chunk: int = 1 << 26, threads: int | None = None):
     """Time the oracle (as it stands) on n64 squares64 and n32 squares32
-    samples, in chunks; returns (samples/s, seconds, threads)."""
+    samples, in chunks, on `threads` threads (default: all host cores);
+    returns (samples/s, seconds, threads)."""
     import oracle
 
     key = int(oracle.make_keys(2, 1)[0])
     from paper_2004_06278_gb300 import workloads
 
     base = workloads.throughput_base(3)
-    threads = oracle.default_threads()
+    threads = threads or oracle.default_threads()
     oracle.fill32(key, base, 1 << 16)  # load the library outside the timing
     t0 = time.perf_counter()
     for a in range(0, n64, chunk):
@@ -186,10 +187,13 @@ CPU_SAMPLE = (1 << 28, 1 << 30)  # squares64, squares32 samples: 1/4 of a step
 
 def cpu_baseline_block():
     rate, dt, threads = oracle_sample_rate(*CPU_SAMPLE)
+    rate1, dt1, _ = oracle_sample_rate(CPU_SAMPLE[0] >> 4, CPU_SAMPLE[1] >> 4, threads=1)
     return {"value": rate / 1e9, "unit": "Gsamples/s", "cores": threads, "kind": "oracle",
             "sample": f"2^28 squares64 + 2^30 squares32 samples of the step's workload "
                       f"(1/4 of a step), oracle in 2^26-sample calls on {threads} threads, "
-                      f"{dt:.2f} s wall"}
+                      f"{dt:.2f} s wall",
+            "single_thread": {"value": rate1 / 1e9, "unit": "Gsamples/s",
+                              "sample": f"2^24 squares64 + 2^26 squares32 samples, {dt1:.2f} s wall"}}
 
 
 def reference_arm(args, rank, world):
