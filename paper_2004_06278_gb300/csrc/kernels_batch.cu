@@ -46,7 +46,8 @@ __device__ __forceinline__ uint32_t find_stream(const int64_t *__restrict__ offs
 
 // squares32 of C consecutive counters from y = ctr*key, e = t(ctr+1) - t(ctr)
 // and c2 = 2*key^2: one squaring for round 1, then additions (the
-// recurrence of round1_delta).
+// recurrence of round1_delta): t_{j+1} = t_j + e + j*c2, one three-input
+// addition per counter with e fixed for the chunk.
 template <int C>
 __device__ __forceinline__ void run32(uint64_t y, uint64_t e, uint64_t key, uint64_t c2, uint32_t (&w)[C]) {
     uint64_t t = round1_value(y);
@@ -55,8 +56,7 @@ __device__ __forceinline__ void run32(uint64_t y, uint64_t e, uint64_t key, uint
         const uint64_t z = add64(y, key);
         w[j] = squares32_tyz(t, y, z);
         y = z;
-        t = add64(t, e);
-        e = add64(e, c2);
+        t = add64x3(t, e, c2 * static_cast<uint64_t>(j));
     }
 }
 
