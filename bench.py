@@ -572,19 +572,42 @@ def breakdown(torch, sq, C, workloads, dev, ms32_plain, tuned_from_file=False):
     del outb, keys, bases, lengths, offsets
     torch.cuda.empty_cache()
 
-    # transforms, 2^30 outputs each
+    # transforms, 2^30 outputs each (two floats or one normal pair per
+    # squares64 output for uniform2_f32 / normal_f32)
     key = int(sq.make_keys(11, 1)[0])
     n = 1 << 30
-    buf = torch.empty(n * 4, dtype=torch.uint8, device=dev)
+    buf = torch.empty(n * 8, dtype=torch.uint8, device=dev)
     for name, kid, fn, es in (("uniform_f32", C.SQ_KERNEL_UNIFORM_F32, C.sq_uniform_f32, 4),
                               ("uniform_bf16", C.SQ_KERNEL_UNIFORM_BF16, C.sq_uniform_bf16, 2),
-                              ("normal_f32", C.SQ_KERNEL_NORMAL_F32, C.sq_normal_f32, 4)):
+                              ("normal_f32", C.SQ_KERNEL_NORMAL_F32, C.sq_normal_f32, 4),
+                              ("uniform2_f32", C.SQ_KERNEL_UNIFORM2_F32, C.sq_uniform2_f32, 4),
+                              ("uniform_f64", C.SQ_KERNEL_UNIFORM_F64, C.sq_uniform_f64, 8)):
         if not tuned_from_file:
             C.sq_autotune(kid, n)
         ms = _time_launches(torch, lambda: fn(key, 0, n, buf.data_ptr(), sh()), 10, stream)
         out[name] = {"Gsamples_per_s": n / (ms / 1e3) / 1e9, "GBps": n * es / (ms / 1e3) / 1e9,
                      "ms": ms}
+
+    # strided counters (Section 4's increments other than one), 2^30 outputs
+    for name, fn, es in (("u32_stride3", C.sq_u32_strided, 4), ("u64_stride3", C.sq_u64_strided, 8)):
+        ms = _time_launches(torch, lambda: fn(key, 5, 3, n, buf.data_ptr(), sh()), 10, stream)
+        out[name] = {"Gsamples_per_s": n / (ms / 1e3) / 1e9, "GBps": n * es / (ms / 1e3) / 1e9,
+                     "ms": ms}
     del buf
+    torch.cuda.empty_cache()
+
+    # key-counter mode (Section 4): one output per key at a fixed counter,
+    # 2^27 keys (2^22 distinct keys tiled 32 times: the host key utility
+    # takes ~0.4 us per key); bytes = 8 read + 4 or 8 written per key
+    nk = 1 << 27
+    kk = torch.from_numpy(sq.make_keys(17, 1 << 22).view(np.int64)).to(dev).repeat(nk >> 22)
+    kbuf = torch.empty(nk * 8, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+    for name, fn, es in (("keys_u32", C.sq_keys_u32, 4), ("keys_u64", C.sq_keys_u64, 8)):
+        ms = _time_launches(torch, lambda: fn(kk.data_ptr(), nk, 0, kbuf.data_ptr(), sh()), 10, stream)
+        out[name] = {"Gsamples_per_s": nk / (ms / 1e3) / 1e9, "GBps": nk * (8 + es) / (ms / 1e3) / 1e9,
+                     "ms": ms, "keys": nk, "distinct_keys": 1 << 22}
+    del kk, kbuf
     torch.cuda.empty_cache()
 
     # generation-only statistics, 2^20 streams x 2^18 counters

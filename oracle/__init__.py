@@ -15,6 +15,7 @@ Every function names the paper passage it follows:
   fill32_strided / fill64_strided  strided counters (Section 4)
   uniform_f32 / uniform_bf16 ..... float conversion (Section 5 prose), FP64
   uniform2_f32 / uniform_f64 ..... two floats / one 53-bit double per squares64
+  uniform53_of ................... that double for given 64-bit values
   normal_f64 ..................... Box-Muller on squares64 halves, FP64
   box_muller_f64 ................. the same pair for given 32-bit halves
   fused_stats .................... XOR / top-byte sum / top-byte histogram
@@ -83,6 +84,7 @@ def _load():
             "oracle_uniform_bf16": (None, [_u64, _u64, _u64, _p]),
             "oracle_normal_f64": (None, [_u64, _u64, _u64, _p]),
             "oracle_box_muller_f64": (None, [_p, _p, _u64, _p]),
+            "oracle_uniform53_of": (None, [_p, _u64, _p]),
             "oracle_fused_stats": (None, [_p, _p, _u64, _u64, _p, _p, _p]),
             "oracle_make_keys": (_i, [_u64, _u64, _p]),
             "oracle_splitmix64": (None, [_u64, _u64, _p]),
@@ -273,6 +275,14 @@ def normal_f64(key: int, base: int, n: int, threads: int | None = None) -> np.nd
         lib.oracle_normal_f64(key, (base + a) & M64, count, addr + 8 * 2 * a)
 
     _parallel(run, _chunks(npairs, threads), threads)
+    return out
+
+
+def uniform53_of(v) -> np.ndarray:
+    """floor(v / 2^11) / 2^53 as doubles, for given 64-bit values."""
+    v = np.ascontiguousarray(v, dtype=np.uint64)
+    out = np.empty(v.shape, dtype=np.float64)
+    _load().oracle_uniform53_of(_ptr(v), v.size, _ptr(out))
     return out
 
 

@@ -230,6 +230,12 @@ void oracle_uniform_f64(uint64_t key, uint64_t base, uint64_t n, double *out) {
     }
 }
 
+/* The 53-bit double uniform of given 64-bit values: floor(v / 2^11) / 2^53. */
+void oracle_uniform53_of(const uint64_t *v, uint64_t n, double *out) {
+    uint64_t i;
+    for (i = 0; i < n; ++i) out[i] = (double)(v[i] >> 11) / 9007199254740992.0;
+}
+
 /* The Box-Muller pair from the two 32-bit halves of one squares64 output:
  *   u1 = (hi + 1) / 2^32 in (0, 1],  theta = 2 pi lo / 2^32,
  *   r  = sqrt(-2 ln u1),  z0 = r cos theta,  z1 = r sin theta.

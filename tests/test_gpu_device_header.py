@@ -46,6 +46,17 @@ __global__ void bm_pairs(const uint32_t *hi, const uint32_t *lo, uint64_t n, flo
     out[i] = sq::box_muller(hi[i], lo[i]);
 }
 
+__global__ void u53(const uint64_t *v, uint64_t n, uint64_t *out) {
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = sq::uniform53_bits(v[i]);
+}
+
+extern "C" int run_u53(const uint64_t *v, uint64_t n, uint64_t *out) {
+    u53<<<(unsigned)((n + 255) / 256), 256>>>(v, n, out);
+    return (int)cudaDeviceSynchronize();
+}
+
 extern "C" int run_bm_pairs(const uint32_t *hi, const uint32_t *lo, uint64_t n, float2 *out) {
     bm_pairs<<<(unsigned)((n + 255) / 256), 256>>>(hi, lo, n, out);
     return (int)cudaDeviceSynchronize();
@@ -78,6 +89,7 @@ def consumer(tmp_path_factory):
     lib.run_by_counter.argtypes = [u64, u64, u64, p, p, p]
     lib.run_by_stream.argtypes = [u64, u64, u64, u64, u64, p, p]
     lib.run_bm_pairs.argtypes = [p, p, u64, p]
+    lib.run_u53.argtypes = [p, u64, p]
     return lib
 
 
@@ -151,3 +163,25 @@ def test_box_muller_edges(gpu_lib, consumer):
     if (~small).any():
         assert (err[~small] / np.abs(want[~small])).max() <= 1e-5
     assert np.all(np.isfinite(got))
+
+
+def test_uniform53_edges(gpu_lib, consumer):
+    """sq::uniform53_bits at every leading-one position of k = v >> 11
+    (2^j - 1, 2^j, 2^j + 1 and a random value with that leading one),
+    around the switch at k = 2^32, at 0 and all-ones, against the oracle."""
+    import torch
+
+    rng = np.random.default_rng(81)
+    ks = [0, 1, 2, 3]
+    for j in range(1, 53):
+        ks += [(1 << j) - 1, 1 << j, (1 << j) + 1, (1 << j) | int(rng.integers(0, 1 << j))]
+    ks = np.array([k for k in ks if k < (1 << 53)], dtype=np.uint64)
+    low = rng.integers(0, 1 << 11, ks.size, dtype=np.uint64)  # bits dropped by >> 11
+    v = np.concatenate([(ks << np.uint64(11)) | low, np.array([(1 << 64) - 1], dtype=np.uint64),
+                        rng.integers(0, 1 << 64, 100_000, dtype=np.uint64)])
+    d_v = torch.from_numpy(v.view(np.int64)).cuda()
+    out = torch.empty(v.size, dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+    assert consumer.run_u53(d_v.data_ptr(), v.size, out.data_ptr()) == 0
+    got = out.cpu().numpy().view(np.uint64)
+    assert np.array_equal(got, oracle.uniform53_of(v).view(np.uint64))

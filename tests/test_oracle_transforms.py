@@ -77,6 +77,20 @@ def test_normal_polar_form():
     assert np.array_equal(z_odd, z[:7])
 
 
+def test_uniform53_closed_forms():
+    """floor(v / 2^11) / 2^53 at points with known values, and agreement
+    with numpy's exact conversion of 53-bit integers."""
+    M = (1 << 64) - 1
+    v = np.array([0, 2047, 2048, 1 << 63, M, (1 << 43) - 1, 1 << 43, 3 << 62], dtype=np.uint64)
+    want = np.array([0.0, 0.0, 2.0 ** -53, 0.5, 1 - 2.0 ** -53, (2.0 ** 32 - 1) * 2.0 ** -53,
+                     2.0 ** -21, 0.75])
+    assert np.array_equal(oracle.uniform53_of(v), want)
+    r = np.random.default_rng(5).integers(0, 1 << 64, 10_000, dtype=np.uint64)
+    assert np.array_equal(oracle.uniform53_of(r), (r >> np.uint64(11)).astype(np.float64) * 2.0 ** -53)
+    f = oracle.fill64(key(), 3, 1000)
+    assert np.array_equal(oracle.uniform53_of(f), oracle.uniform_f64(key(), 3, 1000))
+
+
 def test_box_muller_pairs_battery():
     """The per-halves form against closed-form points and the polar
     identities (tests/pins.py)."""
