@@ -45,6 +45,30 @@ def test_key_counter_mode(gpu_lib, ctr):
         assert np.array_equal(g.payload(dt), ref(ctrs, keys))
 
 
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 8, 4097, 100_003])
+def test_key_counter_mode_alignments(gpu_lib, n):
+    """Both launch paths of key-counter mode: keys and output 16-byte
+    aligned (for squares32 four keys per thread per step, then the n mod 4
+    tail) and either misaligned (one key per thread)."""
+    import torch
+
+    keys = gpu_lib.make_keys(26, n + 1)
+    ctr = 0xFEDCBA9876543210
+    for koff in (0, 1):  # keys offset by one element: 8-byte aligned only
+        d_keys = to_dev(keys)
+        kptr = d_keys.data_ptr() + 8 * koff
+        k = keys[koff:koff + n]
+        ctrs = np.full(n, ctr, dtype=np.uint64)
+        for fn, elem, dt, ref in ((C.sq_keys_u32, 4, np.uint32, oracle.pairs32),
+                                  (C.sq_keys_u64, 8, np.uint64, oracle.pairs64)):
+            for ooff in (0, elem):
+                g = Guarded(n * elem, ooff)
+                fn(kptr, n, ctr, g.ptr, stream_handle())
+                assert g.guards_intact(), (koff, ooff)
+                assert np.array_equal(g.payload(dt), ref(ctrs, k)), (koff, ooff)
+        torch.cuda.synchronize()
+
+
 @pytest.mark.parametrize("n", [1, 2, 3, 8, 9, 31, 1001, (1 << 20) + 5])
 def test_uniform2_f32(gpu_lib, n):
     key = int(gpu_lib.make_keys(23, 1)[0])

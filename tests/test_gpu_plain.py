@@ -172,3 +172,38 @@ def test_every_variant_into_pinned_host_memory(gpu_lib, kid, fn, dt, ref):
                 assert not got[:off].any() and not got[off + n:].any(), (v, off)
     finally:
         C.sq_set_config(kid, 0, 0, 256, 0)
+
+
+@pytest.mark.parametrize("name", ["st32x2.cs", "bulk64"])
+def test_capture_with_wide_and_bulk_variants(gpu_lib, name):
+    """The launchers' output-memory query (made for the wide and bulk
+    variants) is legal inside a stream capture: capture sq_u32 and sq_u64,
+    replay, compare with the oracle."""
+    import torch
+
+    key = int(gpu_lib.make_keys(13, 1)[0])
+    n = 3 * 152 * 512 * 16 + 5
+    out32 = torch.empty(n, dtype=torch.int32, device="cuda")
+    out64 = torch.empty(n, dtype=torch.int64, device="cuda")
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    try:
+        for kid in (C.SQ_KERNEL_U32, C.SQ_KERNEL_U64):
+            v = [i for i in range(C.sq_num_variants(kid)) if C.sq_variant_name(kid, i) == name][0]
+            C.sq_set_config(kid, 0, v, 256, 0)
+        with torch.cuda.stream(s):
+            C.sq_u32(key, 7, n, out32.data_ptr(), int(s.cuda_stream))
+            C.sq_u64(key, 7, n, out64.data_ptr(), int(s.cuda_stream))
+            s.synchronize()
+            with torch.cuda.graph(g, stream=s):
+                C.sq_u32(key, 7, n, out32.data_ptr(), int(s.cuda_stream))
+                C.sq_u64(key, 7, n, out64.data_ptr(), int(s.cuda_stream))
+        out32.zero_()
+        out64.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(out32.cpu().numpy().view(np.uint32), oracle.fill32(key, 7, n))
+        assert np.array_equal(out64.cpu().numpy().view(np.uint64), oracle.fill64(key, 7, n))
+    finally:
+        C.sq_set_config(C.SQ_KERNEL_U32, 0, 0, 256, 0)
+        C.sq_set_config(C.SQ_KERNEL_U64, 0, 0, 256, 0)
