@@ -31,6 +31,63 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// The same in 32-byte chunks (8 squares32 or 4 squares64 values): elements
+// before the first 32-byte boundary of out and after the last whole chunk
+// are written one per thread; thread t of the grid writes chunks t, t + T,
+// ... Inside a chunk y steps by S = stride*key and z = y + key; round 1
+// (t = y*y + y) advances by round1_delta(y, S) + j * 2S^2 for the chunk's
+// j-th element (one three-input addition), and between a thread's chunks y
+// and that delta jump by T * (elements per chunk) steps.
+template <bool WIDE>
+__global__ void __launch_bounds__(256)
+    strided_vec_kernel(uint64_t key, uint64_t ctr0, uint64_t stride, void *__restrict__ out, uint64_t n,
+                       uint64_t head, uint64_t nvec) {
+    constexpr int EPV = WIDE ? 4 : 8;
+    const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const uint64_t nt = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    const uint64_t tail0 = head + nvec * EPV;
+    auto single = [&](uint64_t e) {
+        const uint64_t y = (ctr0 + e * stride) * key;
+        if constexpr (WIDE)
+            static_cast<uint64_t *>(out)[e] = squares64_yz(y, add64(y, key));
+        else
+            static_cast<uint32_t *>(out)[e] = squares32_yz(y, add64(y, key));
+    };
+    for (uint64_t e = tid; e < head; e += nt) single(e);
+    for (uint64_t e = tail0 + tid; e < n; e += nt) single(e);
+    if (tid >= nvec) return;
+    const uint64_t S = stride * key;
+    const uint64_t c2 = (S * S) << 1;
+    uint64_t y = (ctr0 + (head + tid * EPV) * stride) * key;
+    uint64_t e0 = round1_delta(y, S);
+    const uint64_t ystep = nt * EPV * S;
+    const uint64_t estep = nt * EPV * c2;
+    char *p = reinterpret_cast<char *>(out) + head * (WIDE ? 8 : 4) + tid * 32;
+    const uint64_t pstep = nt * 32;
+    for (uint64_t it = (nvec - tid + nt - 1) / nt; it != 0; --it) {
+        uint32_t w[8];
+        uint64_t yy = y;
+        uint64_t t = round1_value(y);
+#pragma unroll
+        for (int j = 0; j < EPV; ++j) {
+            const uint64_t z = add64(yy, key);
+            if constexpr (WIDE) {
+                const uint64_t v = squares64_tyz(t, yy, z);
+                w[2 * j] = lo32(v);
+                w[2 * j + 1] = hi32(v);
+            } else {
+                w[j] = squares32_tyz(t, yy, z);
+            }
+            yy = add64(yy, S);
+            t = add64x3(t, e0, c2 * static_cast<uint64_t>(j));
+        }
+        store32B<false>(p, w);
+        y = add64(y, ystep);
+        e0 = add64(e0, estep);
+        p += pstep;
+    }
+}
+
 // out[e] = squares(ctr, keys[e]).
 template <bool WIDE>
 __global__ void __launch_bounds__(256)
@@ -89,6 +146,24 @@ unsigned grid_for(uint64_t n, const void *fn) {
 cudaError_t launch_strided(bool wide, uint64_t key, uint64_t ctr_base, uint64_t stride, size_t n,
                            void *out, cudaStream_t stream) {
     if (n == 0) return cudaSuccess;
+    const size_t es = wide ? 8 : 4;
+    const size_t epv = 32 / es;
+    if (n >= 64 * epv) {
+        // whole 32-byte chunks from the first 32-byte boundary of out
+        const uintptr_t addr = reinterpret_cast<uintptr_t>(out);
+        const uint64_t head = ((32 - addr % 32) % 32) / es;
+        const uint64_t nvec = (n - head) / epv;
+        const void *fn = wide ? reinterpret_cast<const void *>(&strided_vec_kernel<true>)
+                              : reinterpret_cast<const void *>(&strided_vec_kernel<false>);
+        const uint64_t full = static_cast<uint64_t>(current_sm_count()) * occupancy(fn, 256, 0);
+        const uint64_t need = (nvec + 255) / 256;
+        const unsigned grid = static_cast<unsigned>(need < full ? need : full);
+        if (wide)
+            strided_vec_kernel<true><<<grid, 256, 0, stream>>>(key, ctr_base, stride, out, n, head, nvec);
+        else
+            strided_vec_kernel<false><<<grid, 256, 0, stream>>>(key, ctr_base, stride, out, n, head, nvec);
+        return cudaGetLastError();
+    }
     if (wide) {
         strided_kernel<true><<<grid_for(n, reinterpret_cast<const void *>(&strided_kernel<true>)), 256, 0,
                                stream>>>(key, ctr_base, stride, out, n);
