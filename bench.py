@@ -185,6 +185,21 @@ def oracle_sample_rate(n64: int, n32: int, chunk: int = 1 << 26, threads: int | 
 CPU_SAMPLE = (1 << 28, 1 << 30)  # squares64, squares32 samples: 1/4 of a step
 
 
+def cpu_model() -> str:
+    """Host CPU model name (lscpu), for the record beside the oracle timing."""
+    import platform
+    import subprocess
+
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline_block():
     rate, dt, threads = oracle_sample_rate(*CPU_SAMPLE)
     rate1, dt1, _ = oracle_sample_rate(CPU_SAMPLE[0] >> 4, CPU_SAMPLE[1] >> 4, threads=1)
@@ -192,6 +207,7 @@ def cpu_baseline_block():
             "sample": f"2^28 squares64 + 2^30 squares32 samples of the step's workload "
                       f"(1/4 of a step), oracle in 2^26-sample calls on {threads} threads, "
                       f"{dt:.2f} s wall",
+            "cpu_model": cpu_model(),
             "single_thread": {"value": rate1 / 1e9, "unit": "Gsamples/s",
                               "sample": f"2^24 squares64 + 2^26 squares32 samples, {dt1:.2f} s wall"}}
 
