@@ -200,3 +200,34 @@ def test_tune_file_from_environment(lib, tmp_path):
                            env=env, timeout=120)
         assert r.returncode == 0, r.stderr
         assert r.stdout.strip() == want, (path, r.stdout)
+
+
+def test_last_error_is_per_thread(lib):
+    """Each host thread sees its own last error: a failing call in one
+    thread leaves another thread's message untouched."""
+    import threading
+
+    seen = {}
+    started = threading.Barrier(2)
+    failed = threading.Event()
+
+    def failing():
+        started.wait()
+        with pytest.raises(sq.SquaresError):
+            sq.sq_u64(1, 0, 10, 0)
+        seen["failing"] = sq.sq_last_error()
+        failed.set()
+
+    def clean():
+        started.wait()
+        sq.sq_u32(1, 0, 0, 0)  # n = 0: succeeds, clears this thread's message
+        failed.wait(10)
+        seen["clean"] = sq.sq_last_error()
+
+    ts = [threading.Thread(target=failing), threading.Thread(target=clean)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join(30)
+    assert "NULL" in seen["failing"]
+    assert seen["clean"] == ""
