@@ -71,6 +71,7 @@ def _load():
             "oracle_squares64": (_u64, [_u64, _u64]),
             "oracle_squares_w": (_u64, [_u64, _u64, _u, _u, _i, _i]),
             "oracle_hist_w": (None, [_u64, _u, _u, _i, _p]),
+            "oracle_hist_w_range": (None, [_u64, _u, _u, _i, _u64, _u64, _p]),
             "oracle_fill32": (None, [_u64, _u64, _u64, _p]),
             "oracle_fill64": (None, [_u64, _u64, _u64, _p]),
             "oracle_fill32_strided": (None, [_u64, _u64, _u64, _u64, _p]),
@@ -145,11 +146,26 @@ def squares_w(ctr: int, key: int, w: int, rounds: int, use_z: bool = True,
     return int(_load().oracle_squares_w(ctr, key, w, rounds, int(use_z), int(wide)))
 
 
-def hist_w(key: int, w: int, rounds: int = 4, use_z: bool = True) -> np.ndarray:
-    """Histogram of the narrow reduced-width output over all 2^w counters."""
-    h = np.zeros(1 << (w // 2), dtype=np.uint64)
-    _load().oracle_hist_w(key, w, rounds, int(use_z), _ptr(h))
-    return h
+def hist_w(key: int, w: int, rounds: int = 4, use_z: bool = True,
+           threads: int | None = None) -> np.ndarray:
+    """Histogram of the narrow reduced-width output over all 2^w counters
+    (counter ranges on worker threads, one histogram each, summed)."""
+    lib = _load()
+    threads = threads or default_threads()
+    ranges = _chunks(1 << w, threads, min_chunk=1 << 22)
+    hs = [np.zeros(1 << (w // 2), dtype=np.uint64) for _ in ranges]
+
+    def run(i):
+        a, b = ranges[i]
+        lib.oracle_hist_w_range(key, w, rounds, int(use_z), a, b, _ptr(hs[i]))
+
+    if len(ranges) <= 1:
+        for i in range(len(ranges)):
+            run(i)
+    else:
+        with ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(run, range(len(ranges))))
+    return np.sum(hs, axis=0, dtype=np.uint64)
 
 
 def fill32(key: int, base: int, n: int, threads: int | None = None) -> np.ndarray:

@@ -103,14 +103,20 @@ uint64_t oracle_squares_w(uint64_t ctr, uint64_t key, unsigned w,
     }
 }
 
+/* Adds to hist (2^(w/2) bins) the reduced-width narrow outputs of the
+ * counters c0 .. c1 - 1 for one key. */
+void oracle_hist_w_range(uint64_t key, unsigned w, unsigned rounds, int use_z,
+                         uint64_t c0, uint64_t c1, uint64_t *hist) {
+    uint64_t c;
+    for (c = c0; c < c1; ++c) hist[oracle_squares_w(c, key, w, rounds, use_z, 0)] += 1;
+}
+
 /* Exhaustive histogram of the reduced-width narrow output over every
  * counter 0 .. 2^w - 1 for one key; hist has 2^(w/2) bins. */
 void oracle_hist_w(uint64_t key, unsigned w, unsigned rounds, int use_z,
                    uint64_t *hist) {
-    const uint64_t count = (uint64_t)1 << w;
-    uint64_t c;
     memset(hist, 0, sizeof(uint64_t) * ((size_t)1 << (w / 2)));
-    for (c = 0; c < count; ++c) hist[oracle_squares_w(c, key, w, rounds, use_z, 0)] += 1;
+    oracle_hist_w_range(key, w, rounds, use_z, 0, (uint64_t)1 << w, hist);
 }
 
 /* ------------------------------------------------------------------------ */

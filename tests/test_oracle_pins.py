@@ -53,6 +53,17 @@ def test_reduced_width_uniform_w28(rng):
     pins.pin_reduced_width_uniform(oracle.hist_w, rng, w=28, nkeys=1)
 
 
+def test_reduced_width_uniform_w32(rng):
+    """32-bit state, 16-bit output: all 2^32 counters of one odd key (and
+    of its even neighbour)."""
+    pins.pin_reduced_width_uniform(oracle.hist_w, rng, w=32, nkeys=1)
+
+
+def test_hist_w_threads_do_not_change_it(rng):
+    key = pins.reduced_keys(24, 1, rng)[0]
+    assert np.array_equal(oracle.hist_w(key, 24, threads=1), oracle.hist_w(key, 24, threads=7))
+
+
 def test_reduced_width_y_only_is_key_independent(rng):
     """The y-only variant (before (ctr+1)*key was added, per the
     acknowledgements) gives a histogram that does not depend on the odd key:
