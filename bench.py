@@ -225,6 +225,8 @@ def reference_arm(args, rank, world):
     unit = 5 << 20  # 2^20 squares64 + 2^22 squares32
     units = int(max(1, min((N64 + N32) // unit, per_step // unit)))
     n64, n32 = units << 20, units << 22
+    for _ in range(args.warmup):  # untimed, same size as a timed step
+        oracle_sample_rate(n64, n32)
     times = []
     for _ in range(args.steps):
         _, dt, threads = oracle_sample_rate(n64, n32)
