@@ -66,7 +66,8 @@ def parse_args():
     p.add_argument("--tune-file", help="load the launch table from this file if it exists "
                                        "(no tuning); otherwise tune and save it there")
     p.add_argument("--profile", choices=["u32", "u64", "batch", "uniform_f32", "uniform_bf16",
-                                         "normal_f32", "uniform2_f32", "uniform_f64", "fused"],
+                                         "normal_f32", "uniform2_f32", "uniform_f64", "fused",
+                                         "u32_stride3", "u64_stride3", "keys_u32", "keys_u64"],
                    help="run one kernel on a small case (for ncu) instead of the benchmark")
     p.add_argument("--profile-n", type=int, default=1 << 28)
     p.add_argument("--reference-budget-s", type=float, default=60.0,
@@ -701,6 +702,8 @@ def profile_case(args):
             "uniform2_f32": C.SQ_KERNEL_UNIFORM2_F32, "uniform_f64": C.SQ_KERNEL_UNIFORM_F64,
             "uniform_f32": C.SQ_KERNEL_UNIFORM_F32, "uniform_bf16": C.SQ_KERNEL_UNIFORM_BF16,
             "normal_f32": C.SQ_KERNEL_NORMAL_F32, "fused": C.SQ_KERNEL_FUSED}
+    if args.profile in ("u32_stride3", "u64_stride3", "keys_u32", "keys_u64"):
+        return profile_next_rows(args, torch, sq, C, dev, sh, n, key)
     if args.tune_file and os.path.exists(args.tune_file):
         # use the configuration tuned for the benchmark's size of this kernel
         C.sq_autotune_load(args.tune_file)
@@ -737,6 +740,29 @@ def profile_case(args):
         es = {"u64": 8, "uniform_bf16": 2, "uniform_f64": 8}.get(args.profile, 4)
         out = torch.empty(n * es, dtype=torch.uint8, device=dev)
         run = lambda: fn(key, base, n, out.data_ptr(), sh)  # noqa: E731
+    for _ in range(5):
+        run()
+    torch.cuda.synchronize()
+    print(f"profile case {args.profile} n={n} done", flush=True)
+    return 0
+
+
+def profile_next_rows(args, torch, sq, C, dev, sh, n, key):
+    """Strided counters (stride 3) and key-counter mode: fixed launch shapes,
+    no tuning table. Key-counter mode uses n / 4 keys (2^22 distinct, tiled)."""
+    import numpy as np
+
+    if args.profile.startswith("keys"):
+        nk = max(1 << 22, n >> 2)
+        k = torch.from_numpy(sq.make_keys(17, 1 << 22).view(np.int64)).to(dev).repeat(nk >> 22)
+        nk = k.numel()
+        out = torch.empty(nk * 8, dtype=torch.uint8, device=dev)
+        fn = C.sq_keys_u32 if args.profile == "keys_u32" else C.sq_keys_u64
+        run = lambda: fn(k.data_ptr(), nk, 0, out.data_ptr(), sh)  # noqa: E731
+    else:
+        fn = C.sq_u32_strided if args.profile == "u32_stride3" else C.sq_u64_strided
+        out = torch.empty(n * 8, dtype=torch.uint8, device=dev)
+        run = lambda: fn(key, 5, 3, n, out.data_ptr(), sh)  # noqa: E731
     for _ in range(5):
         run()
     torch.cuda.synchronize()
