@@ -2,7 +2,9 @@
 tests Section 4 lists (BigCrush and PractRand themselves are not available):
 byte chi-square of one stream, counters with increments other than one,
 key-counter mode (counter fixed at 0), bit-reversed words, correlation
-between the streams of adjacent keys, per-bit frequencies. Each flags only
+between the streams of adjacent keys, per-bit frequencies, and three
+classical tests of the kind those batteries contain (birthday spacings,
+serial correlation at small lags, maximum-of-t). Each flags only
 gross failures (|z| > 6). The generator is produced through the C ABI; the
 histograms are counted on the device with torch."""
 import numpy as np
@@ -100,3 +102,50 @@ def test_adjacent_key_streams_uncorrelated(gpu_lib):
     assert abs(corr) < 6 / np.sqrt(n)
     x = _gen(C.sq_u32, int(keys[0]), 0, n=n) ^ _gen(C.sq_u32, int(keys[1]), 0, n=n)
     assert abs(_bytes_chi2(x)) < 6
+
+
+def test_birthday_spacings(gpu_lib):
+    """Marsaglia's birthday spacings on the 32-bit outputs: 4096 trials of
+    m = 4096 birthdays in a year of 2^32 days; the number of repeated
+    spacings in a trial is about Poisson(m^3 / (4 * 2^32)) = Poisson(4), so
+    the total over the trials is about Poisson(16384)."""
+    import torch
+
+    key = int(gpu_lib.make_keys(56, 1)[0])
+    m, trials = 4096, 4096
+    t = _gen(C.sq_u32, key, 7, n=m * trials).view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+    days = torch.sort(t.view(trials, m), dim=1).values
+    spacings = torch.sort(days[:, 1:] - days[:, :-1], dim=1).values
+    repeats = int((spacings[:, 1:] == spacings[:, :-1]).sum().item())
+    lam = trials * m ** 3 / (4.0 * 2 ** 32)
+    assert abs(repeats - lam) < 6 * np.sqrt(lam), (repeats, lam)
+
+
+def test_serial_correlation_lags(gpu_lib):
+    """Correlation of the uniforms u_i and u_{i+k} for k = 1..8 over 2^28
+    values: each within 6 / sqrt(n) of zero."""
+    import torch
+
+    key = int(gpu_lib.make_keys(57, 1)[0])
+    n = 1 << 28
+    u = _gen(C.sq_uniform_f32, key, 0, n=n).view(torch.float32).double()
+    u = u - u.mean()
+    var = float((u * u).mean())
+    for k in range(1, 9):
+        r = float((u[:-k] * u[k:]).mean()) / var
+        assert abs(r) < 6 / np.sqrt(n), (k, r)
+
+
+def test_maximum_of_eight(gpu_lib):
+    """Maximum-of-t with t = 8: the largest of 8 consecutive uniforms has
+    distribution function x^8, so its 8th power is uniform; chi-square over
+    256 equal bins of 2^25 maxima."""
+    import torch
+
+    key = int(gpu_lib.make_keys(58, 1)[0])
+    groups = 1 << 25
+    u = _gen(C.sq_uniform_f32, key, 11, n=8 * groups).view(torch.float32).double()
+    mx = u.view(groups, 8).max(dim=1).values
+    v = mx ** 8
+    counts = torch.bincount(torch.clamp((v * 256).to(torch.int64), max=255), minlength=256)
+    assert abs(chi2_dev(counts.cpu().numpy(), groups)) < 6
