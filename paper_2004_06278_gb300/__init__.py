@@ -23,8 +23,8 @@ from ._lib import (  # noqa: F401  (re-exported C-ABI names)
 
 __all__ = [n for n in dir(_lib) if n.startswith(("sq_", "SQ_"))] + [
     "SquaresError", "load", "make_keys", "u32", "u64", "uniform_f32", "uniform_bf16",
-    "normal_f32", "uniform2_f32", "uniform_f64", "u32_strided", "keys_u32", "batch",
-    "fused_stats"]
+    "normal_f32", "uniform2_f32", "uniform_f64", "u32_strided", "u64_strided", "keys_u32",
+    "keys_u64", "batch", "fused_stats"]
 
 
 def _stream(stream) -> int:
@@ -73,6 +73,7 @@ def u64(key: int, ctr_base: int, n: int, out=None, stream=None, device=None):
 
 
 def uniform_f32(key: int, ctr_base: int, n: int, out=None, stream=None, device=None):
+    """Uniform float32 (squares32 >> 8) * 2^-24 in [0, 1), exact."""
     import torch
 
     out = _out(out, n, torch.float32, device)
@@ -90,6 +91,8 @@ def uniform_bf16(key: int, ctr_base: int, n: int, out=None, stream=None, device=
 
 
 def normal_f32(key: int, ctr_base: int, n: int, out=None, stream=None, device=None):
+    """Box-Muller normals (torch.float32); squares64(ctr_base + j) gives outputs
+    2j and 2j + 1."""
     import torch
 
     out = _out(out, n, torch.float32, device)
@@ -124,12 +127,30 @@ def u32_strided(key: int, ctr_base: int, stride: int, n: int, out=None, stream=N
     return out
 
 
+def u64_strided(key: int, ctr_base: int, stride: int, n: int, out=None, stream=None, device=None):
+    """squares64 at counters ctr_base + i*stride (torch.uint64)."""
+    import torch
+
+    out = _out(out, n, torch.uint64, device)
+    sq_u64_strided(key, ctr_base, stride, n, out.data_ptr(), _stream(stream))
+    return out
+
+
 def keys_u32(keys, ctr: int, out=None, stream=None):
     """squares32(ctr, keys[i]) for a CUDA tensor of keys (key-counter mode)."""
     import torch
 
     out = _out(out, keys.numel(), torch.uint32, keys.device)
     sq_keys_u32(keys.data_ptr(), keys.numel(), ctr, out.data_ptr(), _stream(stream))
+    return out
+
+
+def keys_u64(keys, ctr: int, out=None, stream=None):
+    """squares64(ctr, keys[i]) for a CUDA tensor of keys (key-counter mode)."""
+    import torch
+
+    out = _out(out, keys.numel(), torch.uint64, keys.device)
+    sq_keys_u64(keys.data_ptr(), keys.numel(), ctr, out.data_ptr(), _stream(stream))
     return out
 
 
