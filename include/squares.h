@@ -17,7 +17,13 @@
  *     kernel runs surface at the caller's next synchronisation. Every launch
  *     is legal inside CUDA stream capture.
  *   - Pointers marked [device] must be device (or managed) memory on the
- *     current device; [host] pointers are ordinary host memory.
+ *     current device; [host] pointers are ordinary host memory. Output
+ *     pointers of the generating calls (sq_u32 ... sq_uniform_f64 and
+ *     sq_batch) may also be host memory the device can write (pinned, or
+ *     system memory on a coherent host link): the kernels then store
+ *     straight across the link, with the 32-byte-per-lane store variant
+ *     whatever variant is configured for device memory, since it fills each
+ *     128-byte line in one warp store.
  *   - The caller owns every buffer. No entry point allocates device memory
  *     except sq_autotune (a temporary buffer it frees before returning) and
  *     sq_batch_validate / sq_batch_graph_create (documented there).
