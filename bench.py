@@ -254,11 +254,22 @@ def reference_arm(args, rank, world):
 # --------------------------------------------------------------------------
 # our arm
 
+def _code_only(text: str) -> str:
+    """C/C++/CUDA source without comments and whitespace: what the compiler
+    sees, so that edits to comments do not retire a profile."""
+    import re
+
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return re.sub(r"\s+", "", text)
+
+
 def source_hash(*rel):
+    """Hash of the kernel sources' code (comments and whitespace removed)."""
     h = hashlib.sha256()
     for r in rel:
-        with open(os.path.join(ROOT, r), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, r), encoding="utf-8") as f:
+            h.update(_code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 
