@@ -602,6 +602,34 @@ def breakdown(torch, sq, C, workloads, dev, ms32_plain, tuned_from_file=False):
     del outb, keys, bases, lengths, offsets
     torch.cuda.empty_cache()
 
+    # many short streams: 2^20 streams of log-uniform length in [30, 300)
+    bs = workloads.ragged_batch(1 << 20, seed=7, lo=30, hi=300)
+    keys = torch.from_numpy(sq.make_keys(bs.key_seed, bs.nstreams).view(np.int64)).to(dev)
+    bases = torch.from_numpy(bs.bases.view(np.int64)).to(dev)
+    lengths = torch.from_numpy(bs.lengths).to(dev)
+    offsets = torch.from_numpy(bs.offsets).to(dev)
+    outb = torch.empty(bs.total, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+    saved = C.sq_get_config(C.SQ_KERNEL_BATCH, 0)
+    C.sq_autotune_batch(keys.data_ptr(), bases.data_ptr(), lengths.data_ptr(),
+                        offsets.data_ptr(), bs.nstreams, outb.data_ptr())
+    cfgs = C.sq_get_config(C.SQ_KERNEL_BATCH, 0)
+
+    def run_short():
+        C.sq_batch(keys.data_ptr(), bases.data_ptr(), lengths.data_ptr(), offsets.data_ptr(),
+                   bs.nstreams, outb.data_ptr(), sh())
+
+    ms_s = _time_graph(torch, run_short, 10, stream)
+    rate_s = bs.total / (ms_s / 1e3)
+    out["batched_short_streams"] = {
+        "streams": bs.nstreams, "samples": bs.total, "ms": ms_s, "Gsamples_per_s": rate_s / 1e9,
+        "per_sample_vs_plain": rate_s / plain_rate,
+        "launch": [C.sq_variant_name(2, cfgs.variant), cfgs.block, cfgs.ctas_per_sm],
+        "timing": "CUDA graph of one launch, 10 replays; configuration tuned on this batch"}
+    C.sq_set_config(C.SQ_KERNEL_BATCH, 0, saved.variant, saved.block, saved.ctas_per_sm)
+    del outb, keys, bases, lengths, offsets
+    torch.cuda.empty_cache()
+
     # transforms, 2^30 outputs each (two floats or one normal pair per
     # squares64 output for uniform2_f32 / normal_f32)
     key = int(sq.make_keys(11, 1)[0])

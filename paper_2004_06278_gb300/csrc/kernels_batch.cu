@@ -201,15 +201,83 @@ __global__ void __launch_bounds__(512, 4)
     }
 }
 
-constexpr int kBatchVariants = 4;
-const char *kBatchVariantNames[kBatchVariants] = {"st32", "st32.cs", "st32x2", "st32x2.cs"};
+// Streams to lanes, for batches of many short streams: a group of LPS lanes
+// (a warp, or a quarter of one) takes stream s, s + G, ... (G groups in the
+// grid); lane j of the group writes elements j, j + LPS, ... of the stream,
+// so a group's store covers LPS consecutive outputs. The lane's counters are
+// LPS apart and y steps by d = LPS * key. A warp per stream carries round 1
+// by round1_delta(y, d), which grows by 2d^2 per step; with 8 lanes per
+// stream (meant for streams of a few dozen values, a few per lane) round 1 is
+// squared for each value, since the recurrence's setup would cost more (both
+// choices measured). The metadata loads of a stream are the same address for
+// every lane of the group and are issued one stream ahead. Any offsets are accepted, gaps are
+// untouched, and no stream lookup is needed.
+template <int LPS>
+__global__ void __launch_bounds__(512)
+    batch_stream_kernel(const uint64_t *__restrict__ keys, const uint64_t *__restrict__ bases,
+                        const int64_t *__restrict__ lengths, const int64_t *__restrict__ offsets,
+                        uint32_t S, uint32_t *__restrict__ out) {
+    const uint64_t gt = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const uint32_t j = static_cast<uint32_t>(gt % LPS);
+    const uint64_t groups = (static_cast<uint64_t>(gridDim.x) * blockDim.x) / LPS;
+    // The next stream's metadata is loaded while the current one is written.
+    uint64_t s = gt / LPS;
+    int64_t n_len = 0, n_off = 0;
+    uint64_t n_key = 0, n_base = 0;
+    if (s < S) {
+        n_len = __ldg(lengths + s);
+        n_off = __ldg(offsets + s);
+        n_key = __ldg(keys + s);
+        n_base = __ldg(bases + s);
+    }
+    for (; s < S; s += groups) {
+        const int64_t len = n_len;
+        const int64_t off = n_off;
+        const uint64_t key = n_key;
+        const uint64_t base = n_base;
+        if (s + groups < S) {
+            n_len = __ldg(lengths + s + groups);
+            n_off = __ldg(offsets + s + groups);
+            n_key = __ldg(keys + s + groups);
+            n_base = __ldg(bases + s + groups);
+        }
+        if (len <= static_cast<int64_t>(j)) continue;
+        uint32_t *o = out + off;
+        uint64_t y = (base + j) * key;
+        const uint64_t d = key * LPS;
+        if constexpr (LPS == 32) {
+            uint64_t t = round1_value(y);
+            uint64_t dt = round1_delta(y, d);
+            const uint64_t ddt = (d * d) << 1;
+            for (int64_t i = j; i < len; i += LPS) {
+                o[i] = squares32_tyz(t, y, add64(y, key));
+                y = add64(y, d);
+                t = add64(t, dt);
+                dt = add64(dt, ddt);
+            }
+        } else {
+            for (int64_t i = j; i < len; i += LPS) {
+                o[i] = squares32_yz(y, add64(y, key));
+                y = add64(y, d);
+            }
+        }
+    }
+}
+
+// Variants 0-3: tiles (8 or 16 elements per thread, default or streaming
+// stores); 4, 5: streams to lanes (32 or 8 lanes per stream).
+constexpr int kBatchVariants = 6;
+const char *kBatchVariantNames[kBatchVariants] = {"st32",        "st32.cs",    "st32x2",
+                                                  "st32x2.cs",   "warp-stream", "lane8-stream"};
 
 const void *batch_fn(int variant) {
     switch (variant) {
         case 0: return reinterpret_cast<const void *>(&batch_kernel<false, 8>);
         case 1: return reinterpret_cast<const void *>(&batch_kernel<true, 8>);
         case 2: return reinterpret_cast<const void *>(&batch_kernel<false, 16>);
-        default: return reinterpret_cast<const void *>(&batch_kernel<true, 16>);
+        case 3: return reinterpret_cast<const void *>(&batch_kernel<true, 16>);
+        case 4: return reinterpret_cast<const void *>(&batch_stream_kernel<32>);
+        default: return reinterpret_cast<const void *>(&batch_stream_kernel<8>);
     }
 }
 
@@ -229,12 +297,19 @@ cudaError_t launch_batch(const Cfg &cfg, const uint64_t *keys, const uint64_t *b
     if (nstreams == 0) return cudaSuccess;
     Cfg c = cfg;
     // Host-resident outputs: contiguous 1 KiB warp stores (see launch_plain).
-    if (c.variant >= 2 && !in_device_memory(out)) c.variant -= 2;
+    if ((c.variant == 2 || c.variant == 3) && !in_device_memory(out)) c.variant -= 2;
     const int ctas = c.ctas_per_sm > 0 ? c.ctas_per_sm : batch_max_ctas_per_sm(c.variant, c.block);
     const unsigned grid = static_cast<unsigned>(current_sm_count()) * static_cast<unsigned>(ctas);
     const uintptr_t addr = reinterpret_cast<uintptr_t>(out);
     const uint32_t head = static_cast<uint32_t>(((32 - (addr % 32)) % 32) / 4);
     const uint32_t S = static_cast<uint32_t>(nstreams);
+    if (c.variant >= 4) {
+        if (c.variant == 4)
+            batch_stream_kernel<32><<<grid, cfg.block, 0, stream>>>(keys, bases, lengths, offsets, S, out);
+        else
+            batch_stream_kernel<8><<<grid, cfg.block, 0, stream>>>(keys, bases, lengths, offsets, S, out);
+        return cudaGetLastError();
+    }
     switch (c.variant) {
         case 0: batch_kernel<false, 8><<<grid, cfg.block, 0, stream>>>(keys, bases, lengths, offsets, S, out, head); break;
         case 1: batch_kernel<true, 8><<<grid, cfg.block, 0, stream>>>(keys, bases, lengths, offsets, S, out, head); break;
