@@ -193,7 +193,9 @@ def test_capture_with_wide_variant(gpu_lib):
     s = torch.cuda.Stream()
     g = torch.cuda.CUDAGraph()
     try:
-        C.sq_set_config(C.SQ_KERNEL_BATCH, 0, C.sq_num_variants(C.SQ_KERNEL_BATCH) - 1, 256, 0)
+        wide = [v for v in range(C.sq_num_variants(C.SQ_KERNEL_BATCH))
+                if C.sq_variant_name(C.SQ_KERNEL_BATCH, v) == "st32x2.cs"][0]
+        C.sq_set_config(C.SQ_KERNEL_BATCH, 0, wide, 256, 0)
         with torch.cuda.stream(s):
             gpu_lib.batch(keys, bases, lengths, offsets, out)
             s.synchronize()
