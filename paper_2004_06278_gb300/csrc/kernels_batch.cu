@@ -205,11 +205,11 @@ __global__ void __launch_bounds__(512, 4)
 // (a warp, or a quarter of one) takes stream s, s + G, ... (G groups in the
 // grid); lane j of the group writes elements j, j + LPS, ... of the stream,
 // so a group's store covers LPS consecutive outputs. The lane's counters are
-// LPS apart and y steps by d = LPS * key. A warp per stream carries round 1
-// by round1_delta(y, d), which grows by 2d^2 per step; with 8 lanes per
-// stream (meant for streams of a few dozen values, a few per lane) round 1 is
-// squared for each value, since the recurrence's setup would cost more (both
-// choices measured). The metadata loads of a stream are the same address for
+// LPS apart and y steps by d = LPS * key. With 32 or 16 lanes per stream
+// round 1 is carried by round1_delta(y, d), which grows by 2d^2 per step;
+// with 8 lanes per stream (meant for streams of a few dozen values, a few
+// per lane) round 1 is squared for each value, since the recurrence's setup
+// would cost more (both choices measured). The metadata loads of a stream are the same address for
 // every lane of the group and are issued one stream ahead. Any offsets are accepted, gaps are
 // untouched, and no stream lookup is needed.
 template <int LPS>
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(512)
         uint32_t *o = out + off;
         uint64_t y = (base + j) * key;
         const uint64_t d = key * LPS;
-        if constexpr (LPS == 32) {
+        if constexpr (LPS >= 16) {
             uint64_t t = round1_value(y);
             uint64_t dt = round1_delta(y, d);
             const uint64_t ddt = (d * d) << 1;
@@ -265,10 +265,11 @@ __global__ void __launch_bounds__(512)
 }
 
 // Variants 0-3: tiles (8 or 16 elements per thread, default or streaming
-// stores); 4, 5: streams to lanes (32 or 8 lanes per stream).
-constexpr int kBatchVariants = 6;
-const char *kBatchVariantNames[kBatchVariants] = {"st32",        "st32.cs",    "st32x2",
-                                                  "st32x2.cs",   "warp-stream", "lane8-stream"};
+// stores); 4-6: streams to lanes (32, 8 or 16 lanes per stream).
+constexpr int kBatchVariants = 7;
+const char *kBatchVariantNames[kBatchVariants] = {"st32",        "st32.cs",      "st32x2",
+                                                  "st32x2.cs",   "warp-stream",  "lane8-stream",
+                                                  "lane16-stream"};
 
 const void *batch_fn(int variant) {
     switch (variant) {
@@ -277,7 +278,8 @@ const void *batch_fn(int variant) {
         case 2: return reinterpret_cast<const void *>(&batch_kernel<false, 16>);
         case 3: return reinterpret_cast<const void *>(&batch_kernel<true, 16>);
         case 4: return reinterpret_cast<const void *>(&batch_stream_kernel<32>);
-        default: return reinterpret_cast<const void *>(&batch_stream_kernel<8>);
+        case 5: return reinterpret_cast<const void *>(&batch_stream_kernel<8>);
+        default: return reinterpret_cast<const void *>(&batch_stream_kernel<16>);
     }
 }
 
@@ -306,8 +308,10 @@ cudaError_t launch_batch(const Cfg &cfg, const uint64_t *keys, const uint64_t *b
     if (c.variant >= 4) {
         if (c.variant == 4)
             batch_stream_kernel<32><<<grid, cfg.block, 0, stream>>>(keys, bases, lengths, offsets, S, out);
-        else
+        else if (c.variant == 5)
             batch_stream_kernel<8><<<grid, cfg.block, 0, stream>>>(keys, bases, lengths, offsets, S, out);
+        else
+            batch_stream_kernel<16><<<grid, cfg.block, 0, stream>>>(keys, bases, lengths, offsets, S, out);
         return cudaGetLastError();
     }
     switch (c.variant) {

@@ -118,9 +118,10 @@ def test_batch_and_fused_argument_checks(lib):
 def test_config_table(lib):
     assert sq.sq_num_variants(sq.SQ_KERNEL_U32) == 7
     assert sq.sq_variant_name(sq.SQ_KERNEL_U32, 6) == "bulk64"
-    assert sq.sq_num_variants(sq.SQ_KERNEL_BATCH) == 6
+    assert sq.sq_num_variants(sq.SQ_KERNEL_BATCH) == 7
     assert sq.sq_variant_name(sq.SQ_KERNEL_BATCH, 4) == "warp-stream"
     assert sq.sq_variant_name(sq.SQ_KERNEL_BATCH, 5) == "lane8-stream"
+    assert sq.sq_variant_name(sq.SQ_KERNEL_BATCH, 6) == "lane16-stream"
     assert sq.sq_variant_name(sq.SQ_KERNEL_U32, 0) == "st32"
     assert sq.sq_variant_name(sq.SQ_KERNEL_U32, 99) is None
     cfg = sq.sq_get_config(sq.SQ_KERNEL_U64, 1 << 20)
