@@ -67,7 +67,8 @@ def parse_args():
                                        "(no tuning); otherwise tune and save it there")
     p.add_argument("--profile", choices=["u32", "u64", "batch", "uniform_f32", "uniform_bf16",
                                          "normal_f32", "uniform2_f32", "uniform_f64", "fused",
-                                         "u32_stride3", "u64_stride3", "keys_u32", "keys_u64"],
+                                         "u32_stride3", "u64_stride3", "keys_u32", "keys_u64",
+                                         "batch_short"],
                    help="run one kernel on a small case (for ncu) instead of the benchmark")
     p.add_argument("--profile-n", type=int, default=1 << 28)
     p.add_argument("--reference-budget-s", type=float, default=60.0,
@@ -747,6 +748,29 @@ def profile_case(args):
             "normal_f32": C.SQ_KERNEL_NORMAL_F32, "fused": C.SQ_KERNEL_FUSED}
     if args.profile in ("u32_stride3", "u64_stride3", "keys_u32", "keys_u64"):
         return profile_next_rows(args, torch, sq, C, dev, sh, n, key)
+    if args.profile == "batch_short":
+        # 2^20 streams of log-uniform length in [30, 300), in the configuration
+        # sq_autotune_batch picks for this batch (16 lanes per stream, block
+        # 512, 2 CTAs per SM), set directly so that no tuning launch precedes
+        bt = workloads.ragged_batch(1 << 20, seed=7, lo=30, hi=300)
+        k = torch.from_numpy(sq.make_keys(7, bt.nstreams).view(np.int64)).to(dev)
+        bb = torch.from_numpy(bt.bases.view(np.int64)).to(dev)
+        ll = torch.from_numpy(bt.lengths).to(dev)
+        oo = torch.from_numpy(bt.offsets).to(dev)
+        out = torch.empty(bt.total, dtype=torch.int32, device=dev)
+        torch.cuda.synchronize()
+        v = [i for i in range(C.sq_num_variants(C.SQ_KERNEL_BATCH))
+             if C.sq_variant_name(C.SQ_KERNEL_BATCH, i) == "lane16-stream"][0]
+        C.sq_set_config(C.SQ_KERNEL_BATCH, 0, v, 512, 2)
+        c = C.sq_get_config(C.SQ_KERNEL_BATCH, 0)
+        print(f"profile config: {C.sq_variant_name(C.SQ_KERNEL_BATCH, c.variant)} block {c.block} "
+              f"ctas/SM {c.ctas_per_sm}", flush=True)
+        for _ in range(5):
+            C.sq_batch(k.data_ptr(), bb.data_ptr(), ll.data_ptr(), oo.data_ptr(), bt.nstreams,
+                       out.data_ptr(), sh)
+        torch.cuda.synchronize()
+        print(f"profile case batch_short streams={bt.nstreams} samples={bt.total} done", flush=True)
+        return 0
     if args.tune_file and os.path.exists(args.tune_file):
         # use the configuration tuned for the benchmark's size of this kernel
         C.sq_autotune_load(args.tune_file)

@@ -249,7 +249,30 @@ __global__ void __launch_bounds__(512)
             uint64_t t = round1_value(y);
             uint64_t dt = round1_delta(y, d);
             const uint64_t ddt = (d * d) << 1;
-            for (int64_t i = j; i < len; i += LPS) {
+            const uint64_t ddt2 = ddt << 1, ddt3 = ddt2 + ddt, ddt4 = ddt << 2;
+            int64_t i = j;
+            // four values per step: t advances by dt + m*ddt for the m-th
+            // (one three-input addition each), dt by 4*ddt per step
+            for (; i + 3 * LPS < len; i += 4 * LPS) {
+                uint64_t z = add64(y, key);
+                o[i] = squares32_tyz(t, y, z);
+                y = add64(y, d);
+                t = add64(t, dt);
+                z = add64(y, key);
+                o[i + LPS] = squares32_tyz(t, y, z);
+                y = add64(y, d);
+                t = add64x3(t, dt, ddt);
+                z = add64(y, key);
+                o[i + 2 * LPS] = squares32_tyz(t, y, z);
+                y = add64(y, d);
+                t = add64x3(t, dt, ddt2);
+                z = add64(y, key);
+                o[i + 3 * LPS] = squares32_tyz(t, y, z);
+                y = add64(y, d);
+                t = add64x3(t, dt, ddt3);
+                dt = add64(dt, ddt4);
+            }
+            for (; i < len; i += LPS) {
                 o[i] = squares32_tyz(t, y, add64(y, key));
                 y = add64(y, d);
                 t = add64(t, dt);
