@@ -206,8 +206,8 @@ int sq_fused_stats(const uint64_t *keys, const uint64_t *ctr_bases, size_t nstre
 
 typedef struct {
     int32_t variant;     /* kernel body: store width / cache policy, see sq_variant_name;
-                          * for SQ_KERNEL_BATCH 0-3 tile the packed output, 4-6 give each
-                          * stream to 32, 8 or 16 lanes (for many short streams) */
+                          * for SQ_KERNEL_BATCH 0-3 tile the packed output, 4-8 give each
+                          * stream to 32, 8, 16, 4 or 1 lanes (for many short streams) */
     int32_t block;       /* threads per CTA: 128, 256 or 512 */
     int32_t ctas_per_sm; /* persistent grid = SMs * ctas_per_sm; 0 = max resident */
     int32_t reserved;

@@ -207,9 +207,9 @@ __global__ void __launch_bounds__(512, 4)
 // so a group's store covers LPS consecutive outputs. The lane's counters are
 // LPS apart and y steps by d = LPS * key. With 32 or 16 lanes per stream
 // round 1 is carried by round1_delta(y, d), which grows by 2d^2 per step;
-// with 8 lanes per stream (meant for streams of a few dozen values, a few
-// per lane) round 1 is squared for each value, since the recurrence's setup
-// would cost more (both choices measured). The metadata loads of a stream are the same address for
+// with 8 or fewer lanes per stream (meant for streams of a few dozen values
+// or fewer, a few per lane) round 1 is squared for each value, since the
+// recurrence's setup would cost more (both choices measured). The metadata loads of a stream are the same address for
 // every lane of the group and are issued one stream ahead. Any offsets are accepted, gaps are
 // untouched, and no stream lookup is needed.
 template <int LPS>
@@ -288,11 +288,11 @@ __global__ void __launch_bounds__(512)
 }
 
 // Variants 0-3: tiles (8 or 16 elements per thread, default or streaming
-// stores); 4-6: streams to lanes (32, 8 or 16 lanes per stream).
-constexpr int kBatchVariants = 7;
-const char *kBatchVariantNames[kBatchVariants] = {"st32",        "st32.cs",      "st32x2",
-                                                  "st32x2.cs",   "warp-stream",  "lane8-stream",
-                                                  "lane16-stream"};
+// stores); 4-8: streams to lanes (32, 8, 16, 4 or 1 lanes per stream).
+constexpr int kBatchVariants = 9;
+const char *kBatchVariantNames[kBatchVariants] = {"st32",          "st32.cs",      "st32x2",
+                                                  "st32x2.cs",     "warp-stream",  "lane8-stream",
+                                                  "lane16-stream", "lane4-stream", "lane1-stream"};
 
 const void *batch_fn(int variant) {
     switch (variant) {
@@ -302,7 +302,9 @@ const void *batch_fn(int variant) {
         case 3: return reinterpret_cast<const void *>(&batch_kernel<true, 16>);
         case 4: return reinterpret_cast<const void *>(&batch_stream_kernel<32>);
         case 5: return reinterpret_cast<const void *>(&batch_stream_kernel<8>);
-        default: return reinterpret_cast<const void *>(&batch_stream_kernel<16>);
+        case 6: return reinterpret_cast<const void *>(&batch_stream_kernel<16>);
+        case 7: return reinterpret_cast<const void *>(&batch_stream_kernel<4>);
+        default: return reinterpret_cast<const void *>(&batch_stream_kernel<1>);
     }
 }
 
@@ -333,8 +335,12 @@ cudaError_t launch_batch(const Cfg &cfg, const uint64_t *keys, const uint64_t *b
             batch_stream_kernel<32><<<grid, cfg.block, 0, stream>>>(keys, bases, lengths, offsets, S, out);
         else if (c.variant == 5)
             batch_stream_kernel<8><<<grid, cfg.block, 0, stream>>>(keys, bases, lengths, offsets, S, out);
-        else
+        else if (c.variant == 6)
             batch_stream_kernel<16><<<grid, cfg.block, 0, stream>>>(keys, bases, lengths, offsets, S, out);
+        else if (c.variant == 7)
+            batch_stream_kernel<4><<<grid, cfg.block, 0, stream>>>(keys, bases, lengths, offsets, S, out);
+        else
+            batch_stream_kernel<1><<<grid, cfg.block, 0, stream>>>(keys, bases, lengths, offsets, S, out);
         return cudaGetLastError();
     }
     switch (c.variant) {
