@@ -68,7 +68,7 @@ def parse_args():
     p.add_argument("--profile", choices=["u32", "u64", "batch", "uniform_f32", "uniform_bf16",
                                          "normal_f32", "uniform2_f32", "uniform_f64", "fused",
                                          "u32_stride3", "u64_stride3", "keys_u32", "keys_u64",
-                                         "batch_short"],
+                                         "batch_short", "batch_mid"],
                    help="run one kernel on a small case (for ncu) instead of the benchmark")
     p.add_argument("--profile-n", type=int, default=1 << 28)
     p.add_argument("--reference-budget-s", type=float, default=60.0,
@@ -748,6 +748,23 @@ def profile_case(args):
             "normal_f32": C.SQ_KERNEL_NORMAL_F32, "fused": C.SQ_KERNEL_FUSED}
     if args.profile in ("u32_stride3", "u64_stride3", "keys_u32", "keys_u64"):
         return profile_next_rows(args, torch, sq, C, dev, sh, n, key)
+    if args.profile == "batch_mid":
+        # 2^14 streams of log-uniform length in [3e3, 3e4) (mean ~1.2e4), tile
+        # kernel st32.cs, block 128, as many CTAs per SM as fit
+        bt = workloads.ragged_batch(1 << 14, seed=7, lo=3e3, hi=3e4)
+        k = torch.from_numpy(sq.make_keys(7, bt.nstreams).view(np.int64)).to(dev)
+        bb = torch.from_numpy(bt.bases.view(np.int64)).to(dev)
+        ll = torch.from_numpy(bt.lengths).to(dev)
+        oo = torch.from_numpy(bt.offsets).to(dev)
+        out = torch.empty(bt.total, dtype=torch.int32, device=dev)
+        torch.cuda.synchronize()
+        C.sq_set_config(C.SQ_KERNEL_BATCH, 0, 1, 128, 0)
+        for _ in range(5):
+            C.sq_batch(k.data_ptr(), bb.data_ptr(), ll.data_ptr(), oo.data_ptr(), bt.nstreams,
+                       out.data_ptr(), sh)
+        torch.cuda.synchronize()
+        print(f"profile case batch_mid streams={bt.nstreams} samples={bt.total} done", flush=True)
+        return 0
     if args.profile == "batch_short":
         # 2^20 streams of log-uniform length in [30, 300), in the configuration
         # sq_autotune_batch picks for this batch (16 lanes per stream, block
