@@ -117,11 +117,12 @@ int sq_keys_u64(const uint64_t *keys, size_t nkeys, uint64_t ctr, uint64_t *out,
  * For every stream s < nstreams and i < lengths[s]:
  *   out[offsets[s] + i] = squares32(ctr_bases[s] + i mod 2^64, keys[s]).
  * keys, ctr_bases [device, uint64_t[nstreams]]; lengths, offsets [device,
- * int64_t[nstreams]]; out [device, uint32_t].
+ * int64_t[nstreams]]; out [device, uint32_t[offsets[S-1] + lengths[S-1]]].
  * Requirements (not checked by this call, which never reads device memory
  * on the host; see sq_batch_validate): lengths[s] >= 0, offsets[0] >= 0,
  * offsets[s] + lengths[s] <= offsets[s+1]. Positions of out that no stream
- * covers are left untouched. The total extent offsets[S-1] + lengths[S-1]
+ * covers are left untouched. Whatever the inputs, no launch variant writes
+ * outside [0, offsets[S-1] + lengths[S-1]). The total extent offsets[S-1] + lengths[S-1]
  * is read on the device, so the call can be captured once and replayed with
  * new lengths. SQ_EINVAL for NULL arrays with nstreams > 0 or a misaligned
  * pointer; SQ_ERANGE if nstreams > 2^31.

@@ -90,7 +90,7 @@ __device__ __forceinline__ void boundary_chunk(const uint64_t *__restrict__ keys
     }
     int64_t seg_lo = __ldg(offsets + s);
     int64_t seg_hi = seg_lo + __ldg(lengths + s);
-    if (seg_lo <= e0 && e0 + EPV <= seg_hi) {
+    if (seg_lo <= e0 && e0 + EPV <= seg_hi && e0 + EPV <= end) {
         const uint64_t key = __ldg(keys + s);
         const uint64_t y = (__ldg(bases + s) + static_cast<uint64_t>(e0 - seg_lo)) * key;
         uint32_t w[EPV];
@@ -167,7 +167,8 @@ __global__ void __launch_bounds__(512, 4)
         int64_t seg_lo = 0;
         if (s != kNoStream) {
             seg_lo = __ldg(offsets + s);
-            const int64_t seg_hi = seg_lo + __ldg(lengths + s);
+            int64_t seg_hi = seg_lo + __ldg(lengths + s);
+            if (seg_hi > end) seg_hi = end;  // only met when the offsets break the requirements
             if (lo + tile <= seg_hi) {
                 k = (seg_hi - lo) >> shift;
                 if (k > t_stop - t) k = t_stop - t;
@@ -220,6 +221,9 @@ __global__ void __launch_bounds__(512)
     const uint64_t gt = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     const uint32_t j = static_cast<uint32_t>(gt % LPS);
     const uint64_t groups = (static_cast<uint64_t>(gridDim.x) * blockDim.x) / LPS;
+    // Like the tile kernels, write nothing outside [0, end), end the extent
+    // offsets[S-1] + lengths[S-1], whatever the other streams' offsets are.
+    const int64_t end = __ldg(offsets + S - 1) + __ldg(lengths + S - 1);
     // The next stream's metadata is loaded while the current one is written.
     uint64_t s = gt / LPS;
     int64_t n_len = 0, n_off = 0;
@@ -231,8 +235,8 @@ __global__ void __launch_bounds__(512)
         n_base = __ldg(bases + s);
     }
     for (; s < S; s += groups) {
-        const int64_t len = n_len;
         const int64_t off = n_off;
+        const int64_t len = (n_len < end - off) ? n_len : end - off;
         const uint64_t key = n_key;
         const uint64_t base = n_base;
         if (s + groups < S) {
@@ -241,7 +245,7 @@ __global__ void __launch_bounds__(512)
             n_key = __ldg(keys + s + groups);
             n_base = __ldg(bases + s + groups);
         }
-        if (len <= static_cast<int64_t>(j)) continue;
+        if (off < 0 || len <= static_cast<int64_t>(j)) continue;
         uint32_t *o = out + off;
         uint64_t y = (base + j) * key;
         const uint64_t d = key * LPS;

@@ -206,3 +206,51 @@ def test_capture_with_wide_variant(gpu_lib):
         assert np.array_equal(host_u32(out), _expect(b, n_out))
     finally:
         C.sq_set_config(C.SQ_KERNEL_BATCH, 0, 0, 256, 0)
+
+
+def _invalid_batches(rng):
+    """Metadata that breaks sq_batch's requirements in four ways: unsorted
+    offsets, streams overlapping the next ones, negative offsets, and an
+    early stream reaching far past the last one's end."""
+    out = []
+    for kind in range(4):
+        S = 24
+        lengths = rng.integers(0, 400, S).astype(np.int64)
+        if kind == 0:
+            offsets = rng.integers(0, 3000, S).astype(np.int64)
+        elif kind == 1:
+            offsets = np.sort(rng.integers(0, 2000, S)).astype(np.int64)
+            lengths = rng.integers(0, 4000, S).astype(np.int64)
+        elif kind == 2:
+            offsets = rng.integers(-500, 2000, S).astype(np.int64)
+            offsets[-1] = abs(int(offsets[-1]))
+        else:
+            offsets = np.sort(rng.integers(0, 500, S)).astype(np.int64)
+            lengths = rng.integers(0, 50, S).astype(np.int64)
+            lengths[0] = 100_000
+        out.append((offsets, lengths))
+    return out
+
+
+def test_invalid_metadata_stays_inside_the_extent(gpu_lib):
+    """Whatever the offsets, no variant writes outside [0, offsets[S-1] +
+    lengths[S-1]): a buffer of exactly that many elements keeps its guard
+    bytes on both sides (the values inside are not defined)."""
+    rng = np.random.default_rng(71)
+    try:
+        for offsets, lengths in _invalid_batches(rng):
+            S = offsets.size
+            end = int(offsets[-1] + lengths[-1])
+            keys = to_dev(gpu_lib.make_keys(72, S))
+            bases = to_dev(rng.integers(0, 1 << 64, S, dtype=np.uint64))
+            d_len, d_off = to_dev(lengths), to_dev(offsets)
+            for v in range(C.sq_num_variants(C.SQ_KERNEL_BATCH)):
+                for block in (128, 512):
+                    C.sq_set_config(C.SQ_KERNEL_BATCH, 0, v, block, 0)
+                    for off in (0, 3):
+                        g = Guarded(4 * end, 4 * off)
+                        C.sq_batch(keys.data_ptr(), bases.data_ptr(), d_len.data_ptr(), d_off.data_ptr(),
+                                   S, g.ptr, stream_handle())
+                        assert g.guards_intact(), (v, block, off, end)
+    finally:
+        C.sq_set_config(C.SQ_KERNEL_BATCH, 0, 0, 256, 0)
