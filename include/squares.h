@@ -209,7 +209,7 @@ typedef struct {
     int32_t variant;     /* kernel body: store width / cache policy, see sq_variant_name;
                           * for SQ_KERNEL_BATCH 0-3 tile the packed output, 4-8 give each
                           * stream to 32, 8, 16, 4 or 1 lanes (for many short streams) */
-    int32_t block;       /* threads per CTA: 128, 256 or 512 */
+    int32_t block;       /* threads per CTA: 128, 256 or 512 (SQ_KERNEL_BATCH also 64) */
     int32_t ctas_per_sm; /* persistent grid = SMs * ctas_per_sm; 0 = max resident */
     int32_t reserved;
 } sq_launch_config;

@@ -92,7 +92,8 @@ int max_ctas(int kid, int variant, int block) {
 
 bool valid_cfg(int kid, const sq::Cfg &c) {
     return c.variant >= 0 && c.variant < num_variants(kid) &&
-           (c.block == 128 || c.block == 256 || c.block == 512) && c.ctas_per_sm >= 0 &&
+           (c.block == 128 || c.block == 256 || c.block == 512 || (kid == SQ_KERNEL_BATCH && c.block == 64)) &&
+           c.ctas_per_sm >= 0 &&
            c.ctas_per_sm <= 32;
 }
 
@@ -613,7 +614,7 @@ int sq_autotune_batch(const uint64_t *keys, const uint64_t *ctr_bases, const int
     if (e != cudaSuccess) return cuda_fail(e, "sq_autotune_batch");
     float best = 1e30f;
     sq::Cfg best_cfg = table().get(SQ_KERNEL_BATCH, 0);
-    const int blocks[3] = {128, 256, 512};
+    const int blocks[4] = {64, 128, 256, 512};
     const int ctas_opts[4] = {1, 2, 4, 0};
     for (int v = 0; v < sq::batch_num_variants() && e == cudaSuccess; ++v)
         for (int b : blocks) {

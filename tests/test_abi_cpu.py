@@ -137,6 +137,11 @@ def test_config_table(lib):
     with pytest.raises(sq.SquaresError):
         sq.sq_set_config(sq.SQ_KERNEL_U64, 0, 0, 100, 0)
     with pytest.raises(sq.SquaresError):
+        sq.sq_set_config(sq.SQ_KERNEL_U64, 0, 0, 64, 0)  # 64-thread CTAs: batch kernel only
+    sq.sq_set_config(sq.SQ_KERNEL_BATCH, 0, 1, 64, 0)
+    assert sq.sq_get_config(sq.SQ_KERNEL_BATCH, 0).block == 64
+    sq.sq_set_config(sq.SQ_KERNEL_BATCH, 0, 0, 256, 0)
+    with pytest.raises(sq.SquaresError):
         sq.sq_get_config(42, 0)
     with pytest.raises(sq.SquaresError):
         sq.sq_num_variants(-1)

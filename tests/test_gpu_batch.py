@@ -65,7 +65,7 @@ def test_every_launch_config(gpu_lib):
     b = workloads.small_ragged_batch(200, seed=21, max_len=40_000)
     try:
         for v in range(C.sq_num_variants(C.SQ_KERNEL_BATCH)):
-            for block in (128, 256, 512):
+            for block in (64, 128, 256, 512):
                 for ctas in (1, 3, 0):
                     C.sq_set_config(C.SQ_KERNEL_BATCH, 0, v, block, ctas)
                     got, n_out = _run(gpu_lib, b, offset_elems=block % 7)
