@@ -11,10 +11,13 @@
 // a tile that touches a stream boundary, a gap or the end of the batch each
 // thread finds the stream of its own chunk by a galloping search forward;
 // chunks inside one stream still take the vector path and only chunks that
-// straddle a boundary are written element by element. The batch extent offsets[S-1] + lengths[S-1] is read on the
-// device, so the launch needs no host-side knowledge of the lengths and can
-// be captured in a CUDA graph. There are no spin-waits and no inter-CTA
-// communication.
+// straddle a boundary are written element by element. The batch extent
+// offsets[S-1] + lengths[S-1] is read on the device, so the launch needs no
+// host-side knowledge of the lengths and can be captured in a CUDA graph;
+// no write lands outside it, whatever the other streams' offsets. There are no spin-waits and no inter-CTA
+// communication. Batches of many short streams are better served by the
+// streams-to-lanes kernels further down (variants 4-8), which the batch
+// autotuner picks when they win.
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -202,17 +205,18 @@ __global__ void __launch_bounds__(512, 4)
     }
 }
 
-// Streams to lanes, for batches of many short streams: a group of LPS lanes
-// (a warp, or a quarter of one) takes stream s, s + G, ... (G groups in the
-// grid); lane j of the group writes elements j, j + LPS, ... of the stream,
-// so a group's store covers LPS consecutive outputs. The lane's counters are
-// LPS apart and y steps by d = LPS * key. With 32 or 16 lanes per stream
-// round 1 is carried by round1_delta(y, d), which grows by 2d^2 per step;
-// with 8 or fewer lanes per stream (meant for streams of a few dozen values
-// or fewer, a few per lane) round 1 is squared for each value, since the
-// recurrence's setup would cost more (both choices measured). The metadata loads of a stream are the same address for
-// every lane of the group and are issued one stream ahead. Any offsets are accepted, gaps are
-// untouched, and no stream lookup is needed.
+// Streams to lanes, for batches of many short streams: a group of LPS
+// consecutive lanes (32, 16, 8, 4 or 1) takes stream s, s + G, ... (G groups
+// in the grid); lane j of the group writes elements j, j + LPS, ... of the
+// stream, so a group's store covers LPS consecutive outputs. The lane's
+// counters are LPS apart and y steps by d = LPS * key. With 32 or 16 lanes
+// per stream round 1 is carried by round1_delta(y, d), which grows by 2d^2
+// per step, four values per loop iteration; with 8 or fewer lanes per stream
+// (meant for streams of a few dozen values or fewer, a few per lane) round 1
+// is squared for each value, since the recurrence's setup would cost more
+// (both choices measured). A stream's metadata loads are the same address
+// for every lane of the group and are issued one stream ahead. Any offsets
+// are accepted, gaps are untouched, and no stream lookup is needed.
 template <int LPS>
 __global__ void __launch_bounds__(512)
     batch_stream_kernel(const uint64_t *__restrict__ keys, const uint64_t *__restrict__ bases,
