@@ -607,32 +607,12 @@ def breakdown(torch, sq, C, workloads, dev, ms32_plain, tuned_from_file=False):
     del outb, keys, bases, lengths, offsets
     torch.cuda.empty_cache()
 
-    # many short streams: 2^20 streams of log-uniform length in [30, 300)
-    bs = workloads.ragged_batch(1 << 20, seed=7, lo=30, hi=300)
-    keys = torch.from_numpy(sq.make_keys(bs.key_seed, bs.nstreams).view(np.int64)).to(dev)
-    bases = torch.from_numpy(bs.bases.view(np.int64)).to(dev)
-    lengths = torch.from_numpy(bs.lengths).to(dev)
-    offsets = torch.from_numpy(bs.offsets).to(dev)
-    outb = torch.empty(bs.total, dtype=torch.int32, device=dev)
-    torch.cuda.synchronize()
-    saved = C.sq_get_config(C.SQ_KERNEL_BATCH, 0)
-    C.sq_autotune_batch(keys.data_ptr(), bases.data_ptr(), lengths.data_ptr(),
-                        offsets.data_ptr(), bs.nstreams, outb.data_ptr())
-    cfgs = C.sq_get_config(C.SQ_KERNEL_BATCH, 0)
-
-    def run_short():
-        C.sq_batch(keys.data_ptr(), bases.data_ptr(), lengths.data_ptr(), offsets.data_ptr(),
-                   bs.nstreams, outb.data_ptr(), sh())
-
-    ms_s = _time_graph(torch, run_short, 10, stream)
-    rate_s = bs.total / (ms_s / 1e3)
-    out["batched_short_streams"] = {
-        "streams": bs.nstreams, "samples": bs.total, "ms": ms_s, "Gsamples_per_s": rate_s / 1e9,
-        "per_sample_vs_plain": rate_s / plain_rate,
-        "launch": [C.sq_variant_name(2, cfgs.variant), cfgs.block, cfgs.ctas_per_sm],
-        "timing": "CUDA graph of one launch, 10 replays; configuration tuned on this batch"}
-    C.sq_set_config(C.SQ_KERNEL_BATCH, 0, saved.variant, saved.block, saved.ctas_per_sm)
-    del outb, keys, bases, lengths, offsets
+    # mid-length and many short streams, each with the configuration the
+    # batch tuner picks for it (then the long-stream choice is restored)
+    for name, S_, lo_, hi_ in (("batched_mid_streams", 1 << 14, 3e3, 3e4),
+                               ("batched_short_streams", 1 << 20, 30, 300)):
+        out[name] = _batch_regime(torch, sq, C, workloads, np, dev, stream, sh, S_, lo_, hi_,
+                                  plain_rate)
     torch.cuda.empty_cache()
 
     # transforms, 2^30 outputs each (two floats or one normal pair per
@@ -694,6 +674,35 @@ def breakdown(torch, sq, C, workloads, dev, ms32_plain, tuned_from_file=False):
     # context: cuRAND Philox4x32-10 (library call) on the same GPU
     out["curand_philox4x32_10"] = curand_context(torch, dev, stream)
     return out
+
+
+def _batch_regime(torch, sq, C, workloads, np, dev, stream, sh, S, lo, hi, plain_rate):
+    """One ragged batch of S streams of log-uniform length in [lo, hi), timed
+    in the configuration sq_autotune_batch picks for it; the batch kernel's
+    previous configuration is restored afterwards."""
+    bs = workloads.ragged_batch(S, seed=7, lo=lo, hi=hi)
+    keys = torch.from_numpy(sq.make_keys(bs.key_seed, bs.nstreams).view(np.int64)).to(dev)
+    bases = torch.from_numpy(bs.bases.view(np.int64)).to(dev)
+    lengths = torch.from_numpy(bs.lengths).to(dev)
+    offsets = torch.from_numpy(bs.offsets).to(dev)
+    outb = torch.empty(bs.total, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+    saved = C.sq_get_config(C.SQ_KERNEL_BATCH, 0)
+    C.sq_autotune_batch(keys.data_ptr(), bases.data_ptr(), lengths.data_ptr(),
+                        offsets.data_ptr(), bs.nstreams, outb.data_ptr())
+    cfg = C.sq_get_config(C.SQ_KERNEL_BATCH, 0)
+
+    def run():
+        C.sq_batch(keys.data_ptr(), bases.data_ptr(), lengths.data_ptr(), offsets.data_ptr(),
+                   bs.nstreams, outb.data_ptr(), sh())
+
+    ms = _time_graph(torch, run, 10, stream)
+    C.sq_set_config(C.SQ_KERNEL_BATCH, 0, saved.variant, saved.block, saved.ctas_per_sm)
+    rate = bs.total / (ms / 1e3)
+    return {"streams": bs.nstreams, "mean_length": bs.total / bs.nstreams, "samples": bs.total,
+            "ms": ms, "Gsamples_per_s": rate / 1e9, "per_sample_vs_plain": rate / plain_rate,
+            "launch": [C.sq_variant_name(2, cfg.variant), cfg.block, cfg.ctas_per_sm],
+            "timing": "CUDA graph of one launch, 10 replays; configuration tuned on this batch"}
 
 
 def curand_context(torch, dev, stream):
