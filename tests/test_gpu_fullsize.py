@@ -6,7 +6,8 @@ host cores).
   squares64, 2^30 outputs, and squares32, 2^32 outputs, one key (seed 2),
   counter base uniform in [0, 2^64);
   squares32, 2^24 outputs from counter 0, key of seed 1;
-  the ragged batch of 4096 streams (seed 7, wrapping streams);
+  the ragged batch of 4096 streams (seed 7, wrapping streams), and the
+  mid-length (2^14 streams) and short-stream (2^20) batches;
   uniform FP32 / BF16 (exact) and normals (error bounds), 2^30 each;
   generation-only statistics, 2^20 streams x 2^18 counters.
 """
@@ -103,6 +104,35 @@ def test_batched_4096_all_outputs(gpu_lib):
     _compare_chunks(out, b.total, expect, np.uint32)
     del out
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("S,lo,hi", [(1 << 14, 3e3, 3e4), (1 << 20, 30, 300)])
+def test_batched_regimes_all_outputs(gpu_lib, S, lo, hi):
+    """The mid-length and short-stream batches of the benchmark's breakdown,
+    in the configuration the batch tuner picks for each (a tile kernel with
+    64-thread CTAs, a streams-to-lanes kernel): every output against the
+    oracle's batch, which also leaves uncovered positions untouched."""
+    import torch
+
+    b = workloads.ragged_batch(S, seed=7, lo=lo, hi=hi)
+    keys_dev = gpu_lib.make_keys(b.key_seed, b.nstreams)
+    out = torch.empty(b.total, dtype=torch.int32, device="cuda")
+    d_keys, d_bases = to_dev(keys_dev), to_dev(b.bases)
+    d_lengths, d_offsets = to_dev(b.lengths), to_dev(b.offsets)
+    saved = C.sq_get_config(C.SQ_KERNEL_BATCH, 0)
+    try:
+        C.sq_autotune_batch(d_keys.data_ptr(), d_bases.data_ptr(), d_lengths.data_ptr(),
+                            d_offsets.data_ptr(), b.nstreams, out.data_ptr())
+        out.fill_(0)
+        C.sq_batch(d_keys.data_ptr(), d_bases.data_ptr(), d_lengths.data_ptr(), d_offsets.data_ptr(),
+                   b.nstreams, out.data_ptr(), stream_handle())
+        torch.cuda.synchronize()
+    finally:
+        C.sq_set_config(C.SQ_KERNEL_BATCH, 0, saved.variant, saved.block, saved.ctas_per_sm)
+    want = np.zeros(b.total, dtype=np.uint32)
+    oracle.batch32(oracle.make_keys(b.key_seed, b.nstreams), b.bases, b.lengths, b.offsets, want)
+    got = out.cpu().numpy().view(np.uint32)
+    assert np.array_equal(got, want), int(np.nonzero(got != want)[0][0])
 
 
 def test_transforms_2p30(gpu_lib):
