@@ -149,3 +149,20 @@ def test_maximum_of_eight(gpu_lib):
     v = mx ** 8
     counts = torch.bincount(torch.clamp((v * 256).to(torch.int64), max=255), minlength=256)
     assert abs(chi2_dev(counts.cpu().numpy(), groups)) < 6
+
+
+def test_squares64_bytes_and_bits(gpu_lib):
+    """squares64 (Section 5): byte chi-square over 2^28 outputs and the
+    frequency of ones at each of the 64 bit positions."""
+    import torch
+
+    key = int(gpu_lib.make_keys(59, 1)[0])
+    n = 1 << 28
+    out = torch.empty(n, dtype=torch.int64, device="cuda")
+    C.sq_u64(key, 1 << 50, n, out.data_ptr(), stream_handle())
+    torch.cuda.synchronize()
+    assert abs(_bytes_chi2(out)) < 6
+    words = out.view(torch.int32)  # little-endian: low word, then high word
+    for half in (words[0::2], words[1::2]):
+        freq = _bits(half.contiguous())
+        assert np.all(np.abs(freq - 0.5) < 6 * 0.5 / np.sqrt(n)), freq
