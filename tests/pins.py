@@ -160,7 +160,7 @@ def reduced_keys(w: int, n: int, rng) -> list[int]:
     return keys
 
 
-def pin_reduced_width_uniform(hist_w, rng, w=24, nkeys=6):
+def pin_reduced_width_uniform(hist_w, rng, w=24, nkeys=6, spread=0.2):
     """Exhaustive brute force of the w-bit analogue over all 2^w counters:
     with odd keys the w/2-bit output is statistically uniform (Section 2
     footnote: each output has probability 2^-(w/2)); with an even key the
@@ -174,7 +174,7 @@ def pin_reduced_width_uniform(hist_w, rng, w=24, nkeys=6):
         hists.append(h)
         assert abs(chi2_dev(h, 1 << w)) < 6.0, (hex(k), chi2_dev(h, 1 << w))
         e = (1 << w) / h.size
-        assert 0.8 * e < h.min() and h.max() < 1.2 * e
+        assert (1 - spread) * e < h.min() and h.max() < (1 + spread) * e
     for i in range(1, len(hists)):
         assert not np.array_equal(hists[0], hists[i])
     even = hist_w(keys[0] ^ 1, w, 4, True)

@@ -54,9 +54,10 @@ def test_reduced_width_uniform_w28(rng):
 
 
 def test_reduced_width_uniform_w32(rng):
-    """32-bit state, 16-bit output: all 2^32 counters of one odd key (and
-    of its even neighbour)."""
-    pins.pin_reduced_width_uniform(oracle.hist_w, rng, w=32, nkeys=1)
+    """32-bit state, 16-bit output: all 2^32 counters of each of three odd
+    keys (chi-square within 6 sigma, every bin within 5 % of 2^16, the
+    keys' histograms different) and of an even neighbour (non-uniform)."""
+    pins.pin_reduced_width_uniform(oracle.hist_w, rng, w=32, nkeys=3, spread=0.05)
 
 
 def test_hist_w_threads_do_not_change_it(rng):
