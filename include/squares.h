@@ -230,10 +230,14 @@ int sq_set_config(int kernel_id, size_t n, const sq_launch_config *cfg);
  * buffer of at most 2 GiB; must not run during stream capture. */
 int sq_autotune(int kernel_id, size_t n_hint);
 
-/* Tune the ragged-batch kernel on the caller's own batch: every candidate
- * configuration is launched on these device arrays (each launch writes the
+/* Tune the ragged-batch kernel on the caller's own batch: candidate
+ * configurations are launched on these device arrays (each launch writes the
  * same, correct outputs into out) and the fastest becomes the one sq_batch
- * uses. Synchronous; allocates no device memory; must not run during stream
+ * uses. The streams-to-lanes variants are candidates only when the mean
+ * stream length (read back from the batch extent) is at most 8192, and a
+ * variant whose probe (block 256, as many CTAs as fit) takes over 3x the
+ * best time so far is not timed in its other configurations. sq_autotune(SQ_KERNEL_BATCH, n) times the tile variants
+ * only. Synchronous; allocates no device memory; must not run during stream
  * capture. Arguments and errors as for sq_batch. */
 int sq_autotune_batch(const uint64_t *keys, const uint64_t *ctr_bases, const int64_t *lengths,
                       const int64_t *offsets, size_t nstreams, uint32_t *out);

@@ -515,7 +515,10 @@ int sq_autotune(int kernel_id, size_t n_hint) {
     std::vector<sq::Cfg> cands;
     const int blocks[3] = {128, 256, 512};
     const int ctas_opts[4] = {1, 2, 4, 0};
-    for (int v = 0; v < num_variants(kernel_id); ++v)
+    // The batch kernel is tuned here on 64 long streams, where only its tile
+    // variants (0-3) can win; sq_autotune_batch tunes on real batches.
+    const int nv = (kernel_id == SQ_KERNEL_BATCH) ? 4 : num_variants(kernel_id);
+    for (int v = 0; v < nv; ++v)
         for (int b : blocks) {
             const int mx = max_ctas(kernel_id, v, b);
             for (int c : ctas_opts)
@@ -612,27 +615,58 @@ int sq_autotune_batch(const uint64_t *keys, const uint64_t *ctr_bases, const int
     cudaStream_t st;
     e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_fail(e, "sq_autotune_batch");
+    // Mean stream length from the batch extent (two values read back). The
+    // streams-to-lanes variants (4 and up) are candidates only for streams of
+    // at most 8192 values on average: on longer ones a lane group walks a
+    // whole stream alone and cannot win. Each variant is first timed at block
+    // 256 with as many CTAs as fit; if that takes over 3x the best time so
+    // far, its other configurations are not timed.
+    int64_t last_off = 0, last_len = 0;
+    e = cudaMemcpy(&last_off, offsets + nstreams - 1, sizeof(int64_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(&last_len, lengths + nstreams - 1, sizeof(int64_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(st);
+        return cuda_fail(e, "sq_autotune_batch: reading the batch extent");
+    }
+    const double extent = static_cast<double>(last_off + last_len);
+    const bool short_streams = extent > 0 && extent / static_cast<double>(nstreams) <= 8192.0;
     float best = 1e30f;
     sq::Cfg best_cfg = table().get(SQ_KERNEL_BATCH, 0);
     const int blocks[4] = {64, 128, 256, 512};
     const int ctas_opts[4] = {1, 2, 4, 0};
-    for (int v = 0; v < sq::batch_num_variants() && e == cudaSuccess; ++v)
+    const int nv = short_streams ? sq::batch_num_variants() : 4;
+    auto time_cfg = [&](const sq::Cfg &cfg, float *ms) {
+        return time_it(st, 5, [&]() {
+            return sq::launch_batch(cfg, keys, ctr_bases, lengths, offsets, nstreams, out, st);
+        }, ms);
+    };
+    for (int v = 0; v < nv && e == cudaSuccess; ++v) {
+        // probe: block 256, as many CTAs as fit
+        const sq::Cfg probe{v, 256, 0};
+        float ms = 0.f;
+        e = time_cfg(probe, &ms);
+        if (e != cudaSuccess) break;
+        if (ms < best) {
+            best = ms;
+            best_cfg = probe;
+        }
+        if (ms > 3.f * best) continue;
         for (int b : blocks) {
             const int mx = sq::batch_max_ctas_per_sm(v, b);
             for (int c : ctas_opts) {
-                if (c > mx) continue;
+                if (c > mx || (b == 256 && c == 0)) continue;
                 const sq::Cfg cfg{v, b, c};
-                float ms = 0.f;
-                e = time_it(st, 5, [&]() {
-                    return sq::launch_batch(cfg, keys, ctr_bases, lengths, offsets, nstreams, out, st);
-                }, &ms);
+                e = time_cfg(cfg, &ms);
                 if (e != cudaSuccess) break;
                 if (ms < best) {
                     best = ms;
                     best_cfg = cfg;
                 }
             }
+            if (e != cudaSuccess) break;
         }
+    }
     cudaStreamDestroy(st);
     if (e != cudaSuccess) return cuda_fail(e, "sq_autotune_batch: candidate launch");
     table().set(SQ_KERNEL_BATCH, 0, best_cfg);

@@ -88,17 +88,16 @@ def test_batched_4096_all_outputs(gpu_lib):
                b.nstreams, out.data_ptr(), stream_handle())
 
     def expect(a, m):
-        res = np.empty(m, dtype=np.uint32)
-        s0 = int(np.searchsorted(b.offsets, a, side="right") - 1)
-        s = s0
-        while s < b.nstreams and int(b.offsets[s]) < a + m:
-            lo = max(a, int(b.offsets[s]))
-            hi = min(a + m, int(b.offsets[s] + b.lengths[s]))
-            if hi > lo:
-                res[lo - a:hi - a] = oracle.fill32(int(keys_or[s]),
-                                                   (int(b.bases[s]) + lo - int(b.offsets[s])) % (1 << 64),
-                                                   hi - lo)
-            s += 1
+        """The oracle's batch restricted to positions [a, a + m): the streams
+        that meet the window, each clipped to it (its counter base advanced
+        by the clipped prefix), in one call."""
+        ends = b.offsets + b.lengths
+        sel = np.nonzero((b.offsets < a + m) & (ends > a))[0]
+        lo = np.maximum(b.offsets[sel], a)
+        hi = np.minimum(ends[sel], a + m)
+        bases = b.bases[sel] + (lo - b.offsets[sel]).astype(np.uint64)  # wraps modulo 2^64
+        res = np.zeros(m, dtype=np.uint32)
+        oracle.batch32(keys_or[sel], bases, (hi - lo).astype(np.int64), (lo - a).astype(np.int64), res)
         return res
 
     _compare_chunks(out, b.total, expect, np.uint32)
