@@ -208,7 +208,8 @@ int sq_fused_stats(const uint64_t *keys, const uint64_t *ctr_bases, size_t nstre
 typedef struct {
     int32_t variant;     /* kernel body: store width / cache policy, see sq_variant_name;
                           * for SQ_KERNEL_BATCH 0-3 tile the packed output, 4-8 give each
-                          * stream to 32, 8, 16, 4 or 1 lanes (for many short streams) */
+                          * stream to 32, 8, 16, 4 or 1 lanes, 9 lays 32 streams end to
+                          * end per warp (4-9 are for many short streams) */
     int32_t block;       /* threads per CTA: 128, 256 or 512 (SQ_KERNEL_BATCH also 64) */
     int32_t ctas_per_sm; /* persistent grid = SMs * ctas_per_sm; 0 = max resident */
     int32_t reserved;
@@ -233,10 +234,11 @@ int sq_autotune(int kernel_id, size_t n_hint);
 /* Tune the ragged-batch kernel on the caller's own batch: candidate
  * configurations are launched on these device arrays (each launch writes the
  * same, correct outputs into out) and the fastest becomes the one sq_batch
- * uses. The streams-to-lanes variants are candidates only when the mean
- * stream length (read back from the batch extent) is at most 8192, and a
- * variant whose probe (block 256, as many CTAs as fit) takes over 3x the
- * best time so far is not timed in its other configurations. sq_autotune(SQ_KERNEL_BATCH, n) times the tile variants
+ * uses. The streams-to-lanes and flattened-warp variants are candidates
+ * only when the mean stream length (read back from the batch extent) is at
+ * most 8192, and a variant whose probe (block 256, as many CTAs as fit)
+ * takes over 3x the best time so far is not timed in its other
+ * configurations. sq_autotune(SQ_KERNEL_BATCH, n) times the tile variants
  * only. Synchronous; allocates no device memory; must not run during stream
  * capture. Arguments and errors as for sq_batch. */
 int sq_autotune_batch(const uint64_t *keys, const uint64_t *ctr_bases, const int64_t *lengths,

@@ -616,9 +616,9 @@ int sq_autotune_batch(const uint64_t *keys, const uint64_t *ctr_bases, const int
     e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_fail(e, "sq_autotune_batch");
     // Mean stream length from the batch extent (two values read back). The
-    // streams-to-lanes variants (4 and up) are candidates only for streams of
-    // at most 8192 values on average: on longer ones a lane group walks a
-    // whole stream alone and cannot win. Each variant is first timed at block
+    // streams-to-lanes and flattened-warp variants (4 and up) are candidates
+    // only for streams of at most 8192 values on average: on longer ones a
+    // lane group or a warp walks a whole stream alone and cannot win. Each variant is first timed at block
     // 256 with as many CTAs as fit; if that takes over 3x the best time so
     // far, its other configurations are not timed.
     int64_t last_off = 0, last_len = 0;

@@ -16,8 +16,9 @@
 // host-side knowledge of the lengths and can be captured in a CUDA graph;
 // no write lands outside it, whatever the other streams' offsets. There are no spin-waits and no inter-CTA
 // communication. Batches of many short streams are better served by the
-// streams-to-lanes kernels further down (variants 4-8), which the batch
-// autotuner picks when they win.
+// streams-to-lanes kernels (variants 4-8) and the flattened-warp kernel
+// (variant 9) further down, which the batch autotuner picks when they
+// win.
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -295,12 +296,129 @@ __global__ void __launch_bounds__(512)
     }
 }
 
+// One entry of a warp's stream table, for a stream that starts at position
+// P of the warp's value sequence: y0 = (base - P) * key, so that position p
+// has Weyl term y = y0 + p * key; the address of the output of position 0
+// (out + offset - P, as an integer: it may lie before out); the key.
+struct alignas(16) FlatEntry {
+    uint64_t y0;
+    uint64_t dst;
+    uint64_t key;
+    uint64_t pad;
+};
+
+// 1 << r for r < 32, else 0 (shl.b32 clamps the shift amount at 32).
+__device__ __forceinline__ uint32_t window_bit(uint32_t r) {
+    uint32_t v;
+    asm("shl.b32 %0, 1, %1;" : "=r"(v) : "r"(r));
+    return v;
+}
+__device__ __forceinline__ uint32_t window_bit(uint64_t r) {
+    return r < 32 ? window_bit(static_cast<uint32_t>(r)) : 0u;
+}
+
+// The walk of a warp's value sequence, 32 positions per step; Pos is
+// uint32_t when the sequence has fewer than 2^31 values, else uint64_t. Pe
+// is the lane's stream start P, or a sentinel that no window reaches when
+// its stream is empty.
+template <typename Pos>
+__device__ __forceinline__ void flat_walk(const FlatEntry *table, Pos Pe, Pos T, uint32_t lane) {
+    const uint32_t le = 0xFFFFFFFFu >> (31u - lane);
+    uint32_t before = 0xFFFFFFFFu;  // streams started before the window, minus 1
+    for (Pos b = 0; b < T; b += 32) {
+        const uint32_t starts = __reduce_or_sync(0xFFFFFFFFu, window_bit(static_cast<Pos>(Pe - b)));
+        const Pos p = b + lane;
+        const uint32_t k = before + __popc(starts & le);
+        before += __popc(starts);
+        if (p < T) {
+            const FlatEntry &e = table[k];
+            const uint64_t y = e.y0 + static_cast<uint64_t>(p) * e.key;
+            uint32_t *dst = reinterpret_cast<uint32_t *>(e.dst) + p;
+            *dst = squares32_yz(y, add64(y, e.key));
+        }
+    }
+}
+
+// Flattened warps, for batches of streams of a few values to a few hundred:
+// warp w takes streams 32g .. 32g + 31 for g = w, w + W, ... (W warps in the
+// grid). Lane L loads stream 32g + L's metadata (coalesced loads), clamps
+// its length to the extent, and a warp scan of the lengths lays the 32
+// streams' values end to end: stream L owns positions P_L .. P_L + len_L - 1
+// of a sequence of T values. The non-empty streams' entries (FlatEntry) go,
+// in order, to a 32-entry table of the warp in shared memory. The warp then
+// walks the sequence 32 positions per step, lane t taking position
+// p = b + t: each stream that starts inside the step sets one bit (an OR
+// across the warp), so the owner of p is entry (streams started before the
+// step) + (bits set at or below t) - 1, and p's output is squares32 of
+// y = y0 + p * key, stored at dst + p. Every lane of a step does the same
+// work whatever the lengths, and consecutive positions of a stream are
+// consecutive outputs, so the stores stay coalesced; round 1 is squared for
+// each value. Positions are 32-bit unless the 32 streams hold 2^31 values or
+// more. A clamped length is also capped at 2^57 so that the 64-bit scan
+// cannot overflow; every write then lies inside its owner's clamped range,
+// whatever the metadata.
+__global__ void __launch_bounds__(512)
+    batch_flat_kernel(const uint64_t *__restrict__ keys, const uint64_t *__restrict__ bases,
+                      const int64_t *__restrict__ lengths, const int64_t *__restrict__ offsets,
+                      uint32_t S, uint32_t *__restrict__ out) {
+    extern __shared__ FlatEntry flat_tables[];
+    FlatEntry *table = flat_tables + (threadIdx.x & ~31u);
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t stride = ((static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5) * 32;
+    const int64_t end = __ldg(offsets + S - 1) + __ldg(lengths + S - 1);
+    constexpr int64_t kLenCap = int64_t{1} << 57;
+    for (uint64_t g = warp * 32; g < S; g += stride) {
+        const uint64_t s = g + lane;
+        int64_t len = 0, off = 0;
+        uint64_t key = 0, base = 0;
+        if (s < S) {
+            len = __ldg(lengths + s);
+            off = __ldg(offsets + s);
+            key = __ldg(keys + s);
+            base = __ldg(bases + s);
+        }
+        if (off < 0) len = 0;
+        else if (len > end - off) len = end - off;
+        if (len < 0) len = 0;
+        if (len > kLenCap) len = kLenCap;
+        int64_t inc = len;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t o = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+            if (lane >= static_cast<uint32_t>(d)) inc += o;
+        }
+        const int64_t P = inc - len;
+        const int64_t T = __shfl_sync(0xFFFFFFFFu, inc, 31);
+        const uint32_t nonempty = __ballot_sync(0xFFFFFFFFu, len > 0);
+        if (len > 0) {
+            FlatEntry &e = table[__popc(nonempty & ((1u << lane) - 1u))];
+            e.y0 = (base - static_cast<uint64_t>(P)) * key;
+            e.dst = reinterpret_cast<uint64_t>(out) + static_cast<uint64_t>(off - P) * 4u;
+            e.key = key;
+        }
+        __syncwarp();
+        if (T < (int64_t{1} << 31))
+            flat_walk<uint32_t>(table, len > 0 ? static_cast<uint32_t>(P) : 0xC0000000u,
+                                static_cast<uint32_t>(T), lane);
+        else
+            flat_walk<uint64_t>(table, len > 0 ? static_cast<uint64_t>(P) : 0xC000000000000000ull,
+                                static_cast<uint64_t>(T), lane);
+        __syncwarp();
+    }
+}
+
 // Variants 0-3: tiles (8 or 16 elements per thread, default or streaming
-// stores); 4-8: streams to lanes (32, 8, 16, 4 or 1 lanes per stream).
-constexpr int kBatchVariants = 9;
-const char *kBatchVariantNames[kBatchVariants] = {"st32",          "st32.cs",      "st32x2",
-                                                  "st32x2.cs",     "warp-stream",  "lane8-stream",
-                                                  "lane16-stream", "lane4-stream", "lane1-stream"};
+// stores); 4-8: streams to lanes (32, 8, 16, 4 or 1 lanes per stream);
+// 9: flattened warps.
+constexpr int kBatchVariants = 10;
+const char *kBatchVariantNames[kBatchVariants] = {
+    "st32",          "st32.cs",      "st32x2",       "st32x2.cs", "warp-stream",
+    "lane8-stream", "lane16-stream", "lane4-stream", "lane1-stream", "flat-warp"};
+
+size_t batch_smem(int variant, int block) {
+    return variant >= 9 ? static_cast<size_t>(block) * sizeof(FlatEntry) : 0;
+}
 
 const void *batch_fn(int variant) {
     switch (variant) {
@@ -312,7 +430,8 @@ const void *batch_fn(int variant) {
         case 5: return reinterpret_cast<const void *>(&batch_stream_kernel<8>);
         case 6: return reinterpret_cast<const void *>(&batch_stream_kernel<16>);
         case 7: return reinterpret_cast<const void *>(&batch_stream_kernel<4>);
-        default: return reinterpret_cast<const void *>(&batch_stream_kernel<1>);
+        case 8: return reinterpret_cast<const void *>(&batch_stream_kernel<1>);
+        default: return reinterpret_cast<const void *>(&batch_flat_kernel);
     }
 }
 
@@ -324,7 +443,9 @@ const char *batch_variant_name(int variant) {
     return (variant >= 0 && variant < kBatchVariants) ? kBatchVariantNames[variant] : nullptr;
 }
 
-int batch_max_ctas_per_sm(int variant, int block) { return occupancy(batch_fn(variant), block, 0); }
+int batch_max_ctas_per_sm(int variant, int block) {
+    return occupancy(batch_fn(variant), block, batch_smem(variant, block));
+}
 
 cudaError_t launch_batch(const Cfg &cfg, const uint64_t *keys, const uint64_t *bases,
                          const int64_t *lengths, const int64_t *offsets, size_t nstreams,
@@ -338,6 +459,11 @@ cudaError_t launch_batch(const Cfg &cfg, const uint64_t *keys, const uint64_t *b
     const uintptr_t addr = reinterpret_cast<uintptr_t>(out);
     const uint32_t head = static_cast<uint32_t>(((32 - (addr % 32)) % 32) / 4);
     const uint32_t S = static_cast<uint32_t>(nstreams);
+    if (c.variant >= 9) {
+        const size_t smem = batch_smem(c.variant, cfg.block);
+        batch_flat_kernel<<<grid, cfg.block, smem, stream>>>(keys, bases, lengths, offsets, S, out);
+        return cudaGetLastError();
+    }
     if (c.variant >= 4) {
         if (c.variant == 4)
             batch_stream_kernel<32><<<grid, cfg.block, 0, stream>>>(keys, bases, lengths, offsets, S, out);

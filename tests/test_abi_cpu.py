@@ -118,7 +118,7 @@ def test_batch_and_fused_argument_checks(lib):
 def test_config_table(lib):
     assert sq.sq_num_variants(sq.SQ_KERNEL_U32) == 7
     assert sq.sq_variant_name(sq.SQ_KERNEL_U32, 6) == "bulk64"
-    assert sq.sq_num_variants(sq.SQ_KERNEL_BATCH) == 9
+    assert sq.sq_num_variants(sq.SQ_KERNEL_BATCH) == 10
     assert sq.sq_variant_name(sq.SQ_KERNEL_BATCH, 4) == "warp-stream"
     assert sq.sq_variant_name(sq.SQ_KERNEL_BATCH, 5) == "lane8-stream"
     assert sq.sq_variant_name(sq.SQ_KERNEL_BATCH, 6) == "lane16-stream"
