@@ -68,7 +68,7 @@ def parse_args():
     p.add_argument("--profile", choices=["u32", "u64", "batch", "uniform_f32", "uniform_bf16",
                                          "normal_f32", "uniform2_f32", "uniform_f64", "fused",
                                          "u32_stride3", "u64_stride3", "keys_u32", "keys_u64",
-                                         "batch_short", "batch_mid"],
+                                         "batch_short", "batch_tiny", "batch_mid"],
                    help="run one kernel on a small case (for ncu) instead of the benchmark")
     p.add_argument("--profile-n", type=int, default=1 << 28)
     p.add_argument("--reference-budget-s", type=float, default=60.0,
@@ -610,7 +610,8 @@ def breakdown(torch, sq, C, workloads, dev, ms32_plain, tuned_from_file=False):
     # mid-length and many short streams, each with the configuration the
     # batch tuner picks for it (then the long-stream choice is restored)
     for name, S_, lo_, hi_ in (("batched_mid_streams", 1 << 14, 3e3, 3e4),
-                               ("batched_short_streams", 1 << 20, 30, 300)):
+                               ("batched_short_streams", 1 << 20, 30, 300),
+                               ("batched_tiny_streams", 1 << 22, 3, 30)):
         out[name] = _batch_regime(torch, sq, C, workloads, np, dev, stream, sh, S_, lo_, hi_,
                                   plain_rate)
     torch.cuda.empty_cache()
@@ -757,28 +758,20 @@ def profile_case(args):
             "normal_f32": C.SQ_KERNEL_NORMAL_F32, "fused": C.SQ_KERNEL_FUSED}
     if args.profile in ("u32_stride3", "u64_stride3", "keys_u32", "keys_u64"):
         return profile_next_rows(args, torch, sq, C, dev, sh, n, key)
-    if args.profile == "batch_mid":
-        # 2^14 streams of log-uniform length in [3e3, 3e4) (mean ~1.2e4), tile
-        # kernel st32.cs, block 128, as many CTAs per SM as fit
-        bt = workloads.ragged_batch(1 << 14, seed=7, lo=3e3, hi=3e4)
-        k = torch.from_numpy(sq.make_keys(7, bt.nstreams).view(np.int64)).to(dev)
-        bb = torch.from_numpy(bt.bases.view(np.int64)).to(dev)
-        ll = torch.from_numpy(bt.lengths).to(dev)
-        oo = torch.from_numpy(bt.offsets).to(dev)
-        out = torch.empty(bt.total, dtype=torch.int32, device=dev)
-        torch.cuda.synchronize()
-        C.sq_set_config(C.SQ_KERNEL_BATCH, 0, 1, 128, 0)
-        for _ in range(5):
-            C.sq_batch(k.data_ptr(), bb.data_ptr(), ll.data_ptr(), oo.data_ptr(), bt.nstreams,
-                       out.data_ptr(), sh)
-        torch.cuda.synchronize()
-        print(f"profile case batch_mid streams={bt.nstreams} samples={bt.total} done", flush=True)
-        return 0
-    if args.profile == "batch_short":
-        # 2^20 streams of log-uniform length in [30, 300), in the configuration
-        # sq_autotune_batch picks for this batch (16 lanes per stream, block
-        # 512, 2 CTAs per SM), set directly so that no tuning launch precedes
-        bt = workloads.ragged_batch(1 << 20, seed=7, lo=30, hi=300)
+    # ragged batches of many streams, each in a fixed launch configuration (set
+    # directly, so that no tuning launch precedes the profiled ones), with
+    # log-uniform lengths in [lo, hi):
+    #   batch_mid:   2^14 streams, [3e3, 3e4) (mean ~1.2e4): tile kernel st32.cs,
+    #                block 128, as many CTAs per SM as fit;
+    #   batch_short: 2^20 streams, [30, 300) (mean ~117): flattened warps,
+    #                block 512, as many CTAs per SM as fit;
+    #   batch_tiny:  2^22 streams, [3, 30) (mean ~11): the same.
+    regimes = {"batch_mid": (1 << 14, 3e3, 3e4, "st32.cs", 128),
+               "batch_short": (1 << 20, 30, 300, "flat-warp", 512),
+               "batch_tiny": (1 << 22, 3, 30, "flat-warp", 512)}
+    if args.profile in regimes:
+        S, lo, hi, vname, block = regimes[args.profile]
+        bt = workloads.ragged_batch(S, seed=7, lo=lo, hi=hi)
         k = torch.from_numpy(sq.make_keys(7, bt.nstreams).view(np.int64)).to(dev)
         bb = torch.from_numpy(bt.bases.view(np.int64)).to(dev)
         ll = torch.from_numpy(bt.lengths).to(dev)
@@ -786,8 +779,8 @@ def profile_case(args):
         out = torch.empty(bt.total, dtype=torch.int32, device=dev)
         torch.cuda.synchronize()
         v = [i for i in range(C.sq_num_variants(C.SQ_KERNEL_BATCH))
-             if C.sq_variant_name(C.SQ_KERNEL_BATCH, i) == "lane16-stream"][0]
-        C.sq_set_config(C.SQ_KERNEL_BATCH, 0, v, 512, 2)
+             if C.sq_variant_name(C.SQ_KERNEL_BATCH, i) == vname][0]
+        C.sq_set_config(C.SQ_KERNEL_BATCH, 0, v, block, 0)
         c = C.sq_get_config(C.SQ_KERNEL_BATCH, 0)
         print(f"profile config: {C.sq_variant_name(C.SQ_KERNEL_BATCH, c.variant)} block {c.block} "
               f"ctas/SM {c.ctas_per_sm}", flush=True)
@@ -795,7 +788,8 @@ def profile_case(args):
             C.sq_batch(k.data_ptr(), bb.data_ptr(), ll.data_ptr(), oo.data_ptr(), bt.nstreams,
                        out.data_ptr(), sh)
         torch.cuda.synchronize()
-        print(f"profile case batch_short streams={bt.nstreams} samples={bt.total} done", flush=True)
+        print(f"profile case {args.profile} streams={bt.nstreams} samples={bt.total} done",
+              flush=True)
         return 0
     if args.tune_file and os.path.exists(args.tune_file):
         # use the configuration tuned for the benchmark's size of this kernel
