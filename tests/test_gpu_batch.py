@@ -208,6 +208,44 @@ def test_capture_with_wide_variant(gpu_lib):
         C.sq_set_config(C.SQ_KERNEL_BATCH, 0, 0, 256, 0)
 
 
+def test_capture_flat_warp_and_replay_with_new_lengths(gpu_lib):
+    """The flattened-warp variant (launched with dynamic shared memory)
+    captured in a CUDA graph: replayed as captured, then again after the
+    lengths were halved on the device, it writes each batch exactly, since
+    the kernel reads the metadata and the extent when it runs."""
+    import types
+
+    import torch
+
+    b = workloads.small_ragged_batch(700, seed=49, max_len=40)
+    keys, bases, lengths, offsets = _device_inputs(gpu_lib, b)
+    n_out = b.total + 9
+    out = filled_u32(n_out, int(FILL))
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    flat = [v for v in range(C.sq_num_variants(C.SQ_KERNEL_BATCH))
+            if C.sq_variant_name(C.SQ_KERNEL_BATCH, v) == "flat-warp"][0]
+    try:
+        C.sq_set_config(C.SQ_KERNEL_BATCH, 0, flat, 128, 0)
+        with torch.cuda.stream(s):
+            gpu_lib.batch(keys, bases, lengths, offsets, out)
+            s.synchronize()
+            with torch.cuda.graph(g, stream=s):
+                gpu_lib.batch(keys, bases, lengths, offsets, out)
+        out.copy_(filled_u32(n_out, int(FILL)))
+        g.replay()
+        assert np.array_equal(host_u32(out), _expect(b, n_out))
+        half = (b.lengths // 2).astype(np.int64)
+        lengths.copy_(to_dev(half))
+        out.copy_(filled_u32(n_out, int(FILL)))
+        g.replay()
+        b2 = types.SimpleNamespace(key_seed=b.key_seed, nstreams=b.nstreams, bases=b.bases,
+                                   lengths=half, offsets=b.offsets)
+        assert np.array_equal(host_u32(out), _expect(b2, n_out))
+    finally:
+        C.sq_set_config(C.SQ_KERNEL_BATCH, 0, 0, 256, 0)
+
+
 def _invalid_batches(rng):
     """Metadata that breaks sq_batch's requirements in four ways: unsorted
     offsets, streams overlapping the next ones, negative offsets, and an

@@ -6,8 +6,10 @@ host cores).
   squares64, 2^30 outputs, and squares32, 2^32 outputs, one key (seed 2),
   counter base uniform in [0, 2^64);
   squares32, 2^24 outputs from counter 0, key of seed 1;
-  the ragged batch of 4096 streams (seed 7, wrapping streams), and the
-  mid-length (2^14 streams) and short-stream (2^20) batches;
+  the ragged batch of 4096 streams (seed 7, wrapping streams), the
+  mid-length (2^14 streams), short (2^20) and very short (2^22) batches,
+  and one flattened-warp group at each side of its 2^31-value switch from
+  32-bit to 64-bit positions;
   uniform FP32 / BF16 (exact) and normals (error bounds), 2^30 each;
   generation-only statistics, 2^20 streams x 2^18 counters.
 """
@@ -105,12 +107,13 @@ def test_batched_4096_all_outputs(gpu_lib):
     torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("S,lo,hi", [(1 << 14, 3e3, 3e4), (1 << 20, 30, 300)])
+@pytest.mark.parametrize("S,lo,hi", [(1 << 14, 3e3, 3e4), (1 << 20, 30, 300), (1 << 22, 3, 30)])
 def test_batched_regimes_all_outputs(gpu_lib, S, lo, hi):
-    """The mid-length and short-stream batches of the benchmark's breakdown,
-    in the configuration the batch tuner picks for each (a tile kernel with
-    64-thread CTAs, a streams-to-lanes kernel): every output against the
-    oracle's batch, which also leaves uncovered positions untouched."""
+    """The mid-length, short and very short stream batches of the
+    benchmark's breakdown, in the configuration the batch tuner picks for
+    each (as measured: a tile kernel with 64-thread CTAs, then flattened
+    warps): every output against the oracle's batch, which also leaves
+    uncovered positions untouched."""
     import torch
 
     b = workloads.ragged_batch(S, seed=7, lo=lo, hi=hi)
@@ -132,6 +135,50 @@ def test_batched_regimes_all_outputs(gpu_lib, S, lo, hi):
     oracle.batch32(oracle.make_keys(b.key_seed, b.nstreams), b.bases, b.lengths, b.offsets, want)
     got = out.cpu().numpy().view(np.uint32)
     assert np.array_equal(got, want), int(np.nonzero(got != want)[0][0])
+
+
+@pytest.mark.parametrize("total", [(1 << 31) - 1, 1 << 31])
+def test_flat_warp_position_widths(gpu_lib, total):
+    """One warp-group of the flattened-warp kernel holding 2^31 - 1 values
+    (its largest 32-bit walk) and 2^31 values (its smallest 64-bit walk):
+    stream 0 of length total - 31 from a counter 2^30 below 2^64 (so it
+    wraps), then 31 streams of one value each. Every output against the
+    oracle, and the 64 words past the extent untouched."""
+    import torch
+
+    from tests.gpu_util import filled_u32
+
+    S = 32
+    keys = gpu_lib.make_keys(13, S)
+    rng = np.random.default_rng(13)
+    bases = rng.integers(0, 1 << 64, S, dtype=np.uint64)
+    bases[0] = np.uint64((1 << 64) - (1 << 30))
+    lengths = np.ones(S, dtype=np.int64)
+    lengths[0] = total - 31
+    offsets = np.zeros(S, dtype=np.int64)
+    offsets[1:] = lengths[0] + np.arange(S - 1)
+    fill = 0xA5A5A5A5
+    out = filled_u32(total + 64, fill)
+    d_keys, d_bases, d_lengths, d_offsets = to_dev(keys), to_dev(bases), to_dev(lengths), to_dev(offsets)
+    flat = [v for v in range(C.sq_num_variants(C.SQ_KERNEL_BATCH))
+            if C.sq_variant_name(C.SQ_KERNEL_BATCH, v) == "flat-warp"][0]
+    saved = C.sq_get_config(C.SQ_KERNEL_BATCH, 0)
+    try:
+        C.sq_set_config(C.SQ_KERNEL_BATCH, 0, flat, 256, 0)
+        C.sq_batch(d_keys.data_ptr(), d_bases.data_ptr(), d_lengths.data_ptr(), d_offsets.data_ptr(),
+                   S, out.data_ptr(), stream_handle())
+        torch.cuda.synchronize()
+    finally:
+        C.sq_set_config(C.SQ_KERNEL_BATCH, 0, saved.variant, saved.block, saved.ctas_per_sm)
+    k0, b0, n0 = int(keys[0]), int(bases[0]), int(lengths[0])
+    _compare_chunks(out, n0, lambda a, m: oracle.fill32(k0, (b0 + a) % (1 << 64), m), np.uint32)
+    tail = out[n0:].cpu().numpy().view(np.uint32)
+    want = np.array([oracle.squares32(int(bases[s]), int(keys[s])) for s in range(1, S)],
+                    dtype=np.uint32)
+    assert np.array_equal(tail[:S - 1], want)
+    assert np.all(tail[S - 1:] == fill)
+    del out
+    torch.cuda.empty_cache()
 
 
 def test_transforms_2p30(gpu_lib):
