@@ -618,9 +618,10 @@ int sq_autotune_batch(const uint64_t *keys, const uint64_t *ctr_bases, const int
     // Mean stream length from the batch extent (two values read back). The
     // streams-to-lanes and flattened-warp variants (4 and up) are candidates
     // only for streams of at most 8192 values on average: on longer ones a
-    // lane group or a warp walks a whole stream alone and cannot win. Each variant is first timed at block
-    // 256 with as many CTAs as fit; if that takes over 3x the best time so
-    // far, its other configurations are not timed.
+    // lane group or a warp walks a whole stream alone and cannot win. Each
+    // variant is first timed at block 256 with as many CTAs as fit; if that
+    // takes over 3x the best time so far, its other configurations are not
+    // timed.
     int64_t last_off = 0, last_len = 0;
     e = cudaMemcpy(&last_off, offsets + nstreams - 1, sizeof(int64_t), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess)
@@ -629,7 +630,7 @@ int sq_autotune_batch(const uint64_t *keys, const uint64_t *ctr_bases, const int
         cudaStreamDestroy(st);
         return cuda_fail(e, "sq_autotune_batch: reading the batch extent");
     }
-    const double extent = static_cast<double>(last_off + last_len);
+    const double extent = static_cast<double>(last_off) + static_cast<double>(last_len);
     const bool short_streams = extent > 0 && extent / static_cast<double>(nstreams) <= 8192.0;
     float best = 1e30f;
     sq::Cfg best_cfg = table().get(SQ_KERNEL_BATCH, 0);

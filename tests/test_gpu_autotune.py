@@ -55,3 +55,26 @@ def test_autotune_batch_on_own_arrays(gpu_lib):
         assert np.array_equal(host_u32(out), want)
     finally:
         C.sq_set_config(C.SQ_KERNEL_BATCH, 0, 0, 256, 0)
+
+
+def test_autotune_batch_long_streams_keeps_tile_variants(gpu_lib):
+    """With more than 8192 values per stream on average the tuner times the
+    tile variants only (0-3): a per-stream lane group or warp is never
+    picked there, whatever the timings. Its pick writes the batch exactly;
+    the output buffer past the extent is left untouched."""
+    b = workloads.small_ragged_batch(40, seed=51, max_len=60_000)
+    assert b.total / b.nstreams > 8192
+    keys = to_dev(gpu_lib.make_keys(b.key_seed, b.nstreams))
+    bases, lengths, offsets = to_dev(b.bases), to_dev(b.lengths), to_dev(b.offsets)
+    fill = 0xA5A5A5A5
+    out = filled_u32(b.total + 5, fill)
+    try:
+        C.sq_autotune_batch(keys.data_ptr(), bases.data_ptr(), lengths.data_ptr(),
+                            offsets.data_ptr(), b.nstreams, out.data_ptr())
+        cfg = C.sq_get_config(C.SQ_KERNEL_BATCH, 0)
+        assert 0 <= cfg.variant < 4, C.sq_variant_name(C.SQ_KERNEL_BATCH, cfg.variant)
+        want = np.full(b.total + 5, fill, dtype=np.uint32)
+        oracle.batch32(oracle.make_keys(b.key_seed, b.nstreams), b.bases, b.lengths, b.offsets, want)
+        assert np.array_equal(host_u32(out), want)
+    finally:
+        C.sq_set_config(C.SQ_KERNEL_BATCH, 0, 0, 256, 0)
