@@ -122,10 +122,10 @@ int sq_keys_u64(const uint64_t *keys, size_t nkeys, uint64_t ctr, uint64_t *out,
  * on the host; see sq_batch_validate): lengths[s] >= 0, offsets[0] >= 0,
  * offsets[s] + lengths[s] <= offsets[s+1]. Positions of out that no stream
  * covers are left untouched. Whatever the inputs, no launch variant writes
- * outside [0, offsets[S-1] + lengths[S-1]). The total extent offsets[S-1] + lengths[S-1]
- * is read on the device, so the call can be captured once and replayed with
- * new lengths. SQ_EINVAL for NULL arrays with nstreams > 0 or a misaligned
- * pointer; SQ_ERANGE if nstreams > 2^31.
+ * outside [0, offsets[S-1] + lengths[S-1]). That extent is read on the
+ * device, so the call can be captured once and replayed with new lengths.
+ * SQ_EINVAL for NULL arrays with nstreams > 0 or a misaligned pointer;
+ * SQ_ERANGE if nstreams > 2^31.
  * ---------------------------------------------------------------------- */
 int sq_batch(const uint64_t *keys, const uint64_t *ctr_bases, const int64_t *lengths,
              const int64_t *offsets, size_t nstreams, uint32_t *out, sq_stream_t stream);

@@ -14,11 +14,11 @@
 // straddle a boundary are written element by element. The batch extent
 // offsets[S-1] + lengths[S-1] is read on the device, so the launch needs no
 // host-side knowledge of the lengths and can be captured in a CUDA graph;
-// no write lands outside it, whatever the other streams' offsets. There are no spin-waits and no inter-CTA
-// communication. Batches of many short streams are better served by the
-// streams-to-lanes kernels (variants 4-8) and the flattened-warp kernel
-// (variant 9) further down, which the batch autotuner picks when they
-// win.
+// no write lands outside it, whatever the other streams' offsets. There are
+// no spin-waits and no inter-CTA communication. Batches of many short
+// streams are better served by the streams-to-lanes kernels (variants 4-8)
+// and the flattened-warp kernel (variant 9) further down, which the batch
+// autotuner picks when they win.
 #include <cuda_runtime.h>
 
 #include "internal.h"
