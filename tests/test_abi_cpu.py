@@ -4,6 +4,7 @@ bad arguments on the host before touching CUDA. No kernel is launched."""
 import ctypes
 import os
 import re
+import subprocess
 
 import numpy as np
 import pytest
@@ -239,3 +240,22 @@ def test_last_error_is_per_thread(lib):
         t.join(30)
     assert "NULL" in seen["failing"]
     assert seen["clean"] == ""
+
+
+def test_device_header_compiles_in_a_consumer(tmp_path):
+    """The public device header builds, for sm_103a, inside a kernel outside
+    the library: the consumer the GPU test runs (squares32 / squares64 by
+    counter and through WeylStream, Box-Muller pairs, 53-bit doubles),
+    compiled here with nvcc without launching anything."""
+    from paper_2004_06278_gb300 import build as libbuild
+    from tests.test_gpu_device_header import CONSUMER
+
+    try:
+        nvcc = libbuild.nvcc()
+    except RuntimeError:
+        pytest.skip("nvcc not available")
+    src = tmp_path / "consumer.cu"
+    src.write_text(CONSUMER)
+    r = subprocess.run([nvcc, *libbuild.ARCH, "-O3", "-std=c++17", "-I", libbuild.INCLUDE, "-c",
+                        str(src), "-o", str(tmp_path / "consumer.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
