@@ -11,6 +11,8 @@ host cores).
   and one flattened-warp group at each side of its 2^31-value switch from
   32-bit to 64-bit positions;
   uniform FP32 / BF16 (exact) and normals (error bounds), 2^30 each;
+  two floats per squares64 output and 53-bit doubles, 2^30 each; strided
+  counters, 2^30 squares32 and squares64; key-counter mode over 2^27 keys;
   generation-only statistics, 2^20 streams x 2^18 counters.
 """
 import numpy as np
@@ -212,6 +214,70 @@ def test_transforms_2p30(gpu_lib):
     C.sq_uniform_bf16(key, 0, n, out16.data_ptr(), stream_handle())
     _compare_chunks(out16, n, lambda a, m: oracle.uniform_bf16(key, a, m), np.uint16)
     del out16
+    torch.cuda.empty_cache()
+
+
+def test_two_floats_and_doubles_2p30(gpu_lib):
+    """Two FP32 uniforms per squares64 output and 53-bit double uniforms,
+    2^30 outputs each (key of seed 11, base 0), tuned as bench.py tunes
+    them: every output bit-exact against the oracle."""
+    import torch
+
+    key = int(gpu_lib.make_keys(11, 1)[0])
+    n = 1 << 30
+    for kid in (C.SQ_KERNEL_UNIFORM2_F32, C.SQ_KERNEL_UNIFORM_F64):
+        C.sq_autotune(kid, n)
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    C.sq_uniform2_f32(key, 0, n, out.data_ptr(), stream_handle())
+    _compare_chunks(out, n, lambda a, m: oracle.uniform2_f32(key, a // 2, m).view(np.uint32),
+                    np.uint32)
+    del out
+    out = torch.empty(n, dtype=torch.int64, device="cuda")
+    C.sq_uniform_f64(key, 0, n, out.data_ptr(), stream_handle())
+    _compare_chunks(out, n, lambda a, m: oracle.uniform_f64(key, a, m).view(np.uint64), np.uint64)
+    del out
+    torch.cuda.empty_cache()
+
+
+def test_strided_2p30(gpu_lib):
+    """Strided counters as the benchmark times them (key of seed 11, base 5,
+    stride 3), 2^30 squares32 and 2^30 squares64 outputs: every output
+    against the oracle."""
+    import torch
+
+    key = int(gpu_lib.make_keys(11, 1)[0])
+    n, base, stride = 1 << 30, 5, 3
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    C.sq_u32_strided(key, base, stride, n, out.data_ptr(), stream_handle())
+    _compare_chunks(out, n, lambda a, m: oracle.fill32_strided(key, base + a * stride, stride, m),
+                    np.uint32)
+    del out
+    out = torch.empty(n, dtype=torch.int64, device="cuda")
+    C.sq_u64_strided(key, base, stride, n, out.data_ptr(), stream_handle())
+    _compare_chunks(out, n, lambda a, m: oracle.fill64_strided(key, base + a * stride, stride, m),
+                    np.uint64)
+    del out
+    torch.cuda.empty_cache()
+
+
+def test_key_counter_2p27_keys(gpu_lib):
+    """Key-counter mode as the benchmark times it: 2^27 keys (the 2^22 keys
+    of seed 17, tiled 32 times) at counter 0, squares32 and squares64, every
+    output against the oracle."""
+    import torch
+
+    nk = 1 << 27
+    keys = np.tile(gpu_lib.make_keys(17, 1 << 22), nk >> 22)
+    d_keys = to_dev(keys)
+    zeros = np.zeros(CHUNK, dtype=np.uint64)
+    out = torch.empty(nk, dtype=torch.int32, device="cuda")
+    C.sq_keys_u32(d_keys.data_ptr(), nk, 0, out.data_ptr(), stream_handle())
+    _compare_chunks(out, nk, lambda a, m: oracle.pairs32(zeros[:m], keys[a:a + m]), np.uint32)
+    del out
+    out = torch.empty(nk, dtype=torch.int64, device="cuda")
+    C.sq_keys_u64(d_keys.data_ptr(), nk, 0, out.data_ptr(), stream_handle())
+    _compare_chunks(out, nk, lambda a, m: oracle.pairs64(zeros[:m], keys[a:a + m]), np.uint64)
+    del out, d_keys
     torch.cuda.empty_cache()
 
 
