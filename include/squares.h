@@ -56,6 +56,13 @@ const char *sq_last_error(void);
 /* Version of this ABI: 100 * major + minor. */
 int sq_abi_version(void);
 
+/* Identifier of the kernel code this library was built from: 16 hex digits
+ * of a hash of the kernel sources' code (comments and whitespace excluded),
+ * or "unknown" when built without it. A tuned launch table is keyed by it
+ * (see sq_autotune_save). Static storage; never NULL. No counterpart in the
+ * paper. */
+const char *sq_build_id(void);
+
 /* Test hook: the next call of the named entry point (e.g. "sq_u32") on the
  * calling thread fails with SQ_ECUDA after its argument checks and before it
  * touches the GPU, as a failed launch would; NULL or "" disarms. Lets a
@@ -148,10 +155,23 @@ int sq_batch_validate(const int64_t *lengths, const int64_t *offsets, size_t nst
  *                  lo = v mod 2^32: u1 = (hi + 1) 2^-32 in (0, 1],
  *                  theta = 2 pi lo 2^-32, r = sqrt(-2 ln u1),
  *                  out[2j] = r cos theta, out[2j+1] = r sin theta; an odd n
- *                  drops the last sine. Computed in FP32 with ln u1 taken
- *                  through log1p of the exact integer complement when
- *                  1 - u1 < 2^-7. Error against the FP64 values: at most 2e-6
- *                  absolute where |z| < 5 and 1e-5 relative beyond.
+ *                  drops the last sine. Computed in FP32 without branches
+ *                  and without CUDA math-library calls: with
+ *                  hi + 1 = 2^E (1 + f), 1 + f in [1/sqrt2, sqrt2),
+ *                  ln u1 = (E - 32) ln 2 + 2 atanh(s), s = D / (hi + 1 + 2^E)
+ *                  where D = hi + 1 - 2^E is formed exactly in 32-bit
+ *                  integers (so s keeps its relative accuracy as u1 -> 1),
+ *                  atanh by its odd Taylor series to s^7; the angle is split
+ *                  into an exact quadrant of lo and a remainder whose sine
+ *                  and cosine come from Taylor series to t^9 / t^8; r from
+ *                  the hardware reciprocal square root plus one Newton step.
+ *                  Error against the FP64 values, measured over all 2^32
+ *                  values of each half: at most 7.5e-7 absolute where
+ *                  |z| < 5 and 1.5e-7 relative beyond (bound stated for
+ *                  callers: 2e-6 absolute, 1e-5 relative).
+ *                  A pointer 4-byte but not 8-byte aligned still gets vector
+ *                  stores: chunks then start at a pair's second element and
+ *                  compute one pair more than they store.
  * out [device], naturally aligned. Errors as for sq_u32.
  * ---------------------------------------------------------------------- */
 int sq_uniform_f32(uint64_t key, uint64_t ctr_base, size_t n, float *out, sq_stream_t stream);
@@ -163,7 +183,8 @@ int sq_normal_f32(uint64_t key, uint64_t ctr_base, size_t n, float *out, sq_stre
  * sq_uniform2_f32: two floats per squares64 output v = squares64(ctr_base+j):
  *                  out[2j] = floor(hi/2^8) 2^-24, out[2j+1] = floor(lo/2^8)
  *                  2^-24 (hi, lo the upper and lower 32 bits); an odd n drops
- *                  the last one. Exact.
+ *                  the last one. Exact. Like sq_normal_f32, a pointer 4-byte
+ *                  but not 8-byte aligned still gets vector stores.
  * sq_uniform_f64:  out[i] = floor(squares64(ctr_base+i) / 2^11) 2^-53, a
  *                  53-bit double in [0, 1), exact; built from integer
  *                  operations (no FP64 arithmetic on the GPU).
@@ -190,9 +211,13 @@ int sq_fused_stats(const uint64_t *keys, const uint64_t *ctr_bases, size_t nstre
 
 /* ------------------------------------------------------------------------
  * Launch configuration and autotuning. Each kernel family has a table of
- * launch configurations indexed by a size bucket (floor(log2(n))); the
- * default entry is a fixed choice for GB300. All variants compute identical
- * results; only the speed differs.
+ * launch configurations indexed by a size bucket (floor(log2(n))): n is the
+ * number of output elements for the plain generators, the total number of
+ * counters for SQ_KERNEL_FUSED, and the number of streams for
+ * SQ_KERNEL_BATCH (so a batch of a few long streams and one of millions of
+ * short ones keep separate choices). The default entry is a fixed choice
+ * for GB300. All variants compute identical results; only the speed
+ * differs.
  * ---------------------------------------------------------------------- */
 #define SQ_KERNEL_U32 0
 #define SQ_KERNEL_U64 1
@@ -227,14 +252,19 @@ int sq_set_config(int kernel_id, size_t n, const sq_launch_config *cfg);
 
 /* Time every candidate configuration on a problem of size n_hint (in output
  * elements; for SQ_KERNEL_FUSED, total counters) and keep the fastest for
- * that size bucket. Synchronous; allocates and frees a temporary device
- * buffer of at most 2 GiB; must not run during stream capture. */
+ * that size bucket. For SQ_KERNEL_BATCH the candidates are the tile
+ * variants on a synthetic batch of 64 long streams holding n_hint elements,
+ * and the pick becomes the entry of every stream-count bucket (calls of
+ * sq_autotune_batch afterwards refine single buckets). Synchronous;
+ * allocates and frees a temporary device buffer of at most 2 GiB; must not
+ * run during stream capture. */
 int sq_autotune(int kernel_id, size_t n_hint);
 
 /* Tune the ragged-batch kernel on the caller's own batch: candidate
  * configurations are launched on these device arrays (each launch writes the
  * same, correct outputs into out) and the fastest becomes the one sq_batch
- * uses. The streams-to-lanes and flattened-warp variants are candidates
+ * uses for batches in the same stream-count bucket (floor(log2(nstreams))).
+ * The streams-to-lanes and flattened-warp variants are candidates
  * only when the mean stream length (read back from the batch extent) is at
  * most 8192, and a variant whose probe (block 256, as many CTAs as fit)
  * takes over 3x the best time so far is not timed in its other
@@ -245,11 +275,27 @@ int sq_autotune_batch(const uint64_t *keys, const uint64_t *ctr_bases, const int
                       const int64_t *offsets, size_t nstreams, uint32_t *out);
 
 /* Persist / restore the tuned table as a small text file keyed by the
- * device name. Loading entries for another device name is a no-op. If the
- * environment variable SQ_TUNE_FILE names such a file, it is loaded on the
- * library's first use of the table. */
+ * device name and by sq_build_id(). Loading a table saved on another
+ * device name is a no-op (SQ_OK). Loading a table saved by a library built
+ * from other kernel code (or a file of format 1, which records no code
+ * identifier) leaves the table unchanged and returns SQ_EINVAL; the message
+ * names both identifiers. If the environment variable SQ_TUNE_FILE names a
+ * file, it is loaded the same way on the library's first use of the table
+ * (a file that does not apply is ignored silently there). */
 int sq_autotune_save(const char *path);
 int sq_autotune_load(const char *path);
+
+/* Store ceiling: writes `value` to out[0..n) with the store path of the
+ * plain generators (the same head / vector-chunk / tail split, persistent
+ * grid and store variant) and no generator arithmetic, so its rate is the
+ * write bandwidth those kernels are held against, for device memory or,
+ * given host memory the device can write, for the host link. cfg selects
+ * the variant, block and CTAs per SM as for SQ_KERNEL_U32 (NULL: the entry
+ * sq_u32 would use for n). out [device or device-writable host], 4-byte
+ * aligned. Errors as for sq_u32, and SQ_EINVAL for an invalid cfg. No
+ * counterpart in the paper: a measurement kernel. */
+int sq_fill_u32(uint32_t value, size_t n, uint32_t *out, const sq_launch_config *cfg,
+                sq_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * CUDA graph of one sq_batch launch, for callers without a graph API of

@@ -15,8 +15,8 @@ from ._lib import (  # noqa: F401  (re-exported C-ABI names)
     SQ_ECUDA, SQ_EINVAL, SQ_ERANGE, SQ_KERNEL_BATCH, SQ_KERNEL_FUSED, SQ_KERNEL_NORMAL_F32,
     SQ_KERNEL_U32, SQ_KERNEL_U64, SQ_KERNEL_UNIFORM2_F32, SQ_KERNEL_UNIFORM_BF16,
     SQ_KERNEL_UNIFORM_F32, SQ_KERNEL_UNIFORM_F64, SQ_NUM_KERNELS, SQ_OK, SquaresError, load,
-    sq_abi_version, sq_autotune, sq_autotune_batch, sq_autotune_load, sq_autotune_save, sq_batch,
-    sq_batch_graph_create, sq_batch_validate, sq_debug_fail_next, sq_fused_stats, sq_get_config, sq_graph_destroy,
+    sq_abi_version, sq_autotune, sq_build_id, sq_autotune_batch, sq_autotune_load, sq_autotune_save, sq_batch,
+    sq_batch_graph_create, sq_batch_validate, sq_debug_fail_next, sq_fill_u32, sq_fused_stats, sq_get_config, sq_graph_destroy,
     sq_graph_launch, sq_keys_u32, sq_keys_u64, sq_last_error, sq_make_keys, sq_normal_f32,
     sq_num_variants, sq_set_config, sq_u32, sq_u32_strided, sq_u64, sq_u64_strided,
     sq_uniform2_f32, sq_uniform_bf16, sq_uniform_f32, sq_uniform_f64, sq_variant_name)

@@ -19,6 +19,10 @@
 #include "internal.h"
 #include "squares.h"
 
+#ifndef SQ_BUILD_ID
+#define SQ_BUILD_ID "unknown"  // build.py passes the hash of the kernel sources' code
+#endif
+
 namespace {
 
 thread_local std::string g_error;
@@ -133,7 +137,10 @@ ConfigTable &raw_table() {
 }
 
 // Reads a table written by sq_autotune_save into the configuration table.
-// Entries tuned for another device name are ignored (SQ_OK).
+// Entries tuned for another device name are ignored (SQ_OK). A table saved
+// by a library built from other kernel code (another sq_build_id, or a
+// version-1 file, which records none) is ignored too, with SQ_EINVAL and a
+// message naming both identifiers: its timings belong to other kernels.
 int load_table_file(const char *path, std::string *err) {
     FILE *f = fopen(path, "r");
     if (!f) {
@@ -142,7 +149,8 @@ int load_table_file(const char *path, std::string *err) {
     }
     char line[512];
     int version = 0;
-    if (!fgets(line, sizeof line, f) || sscanf(line, "squares-autotune %d", &version) != 1 || version != 1) {
+    if (!fgets(line, sizeof line, f) || sscanf(line, "squares-autotune %d", &version) != 1 ||
+        (version != 1 && version != 2)) {
         fclose(f);
         *err = std::string(path) + " is not an autotune file";
         return SQ_EINVAL;
@@ -152,9 +160,20 @@ int load_table_file(const char *path, std::string *err) {
         file_dev = line + 7;
         while (!file_dev.empty() && (file_dev.back() == '\n' || file_dev.back() == '\r')) file_dev.pop_back();
     }
+    std::string file_code = "none";
+    if (version == 2 && fgets(line, sizeof line, f) && strncmp(line, "code ", 5) == 0) {
+        file_code = line + 5;
+        while (!file_code.empty() && (file_code.back() == '\n' || file_code.back() == '\r')) file_code.pop_back();
+    }
     if (file_dev != device_name()) {
         fclose(f);
         return SQ_OK;  // tuned for another device: keep the defaults
+    }
+    if (file_code != SQ_BUILD_ID) {
+        fclose(f);
+        *err = std::string(path) + " was tuned on kernel code " + file_code + ", this library's is " +
+               SQ_BUILD_ID + ": table ignored";
+        return SQ_EINVAL;
     }
     int k, b, v, bl, c;
     std::vector<std::pair<std::pair<int, int>, sq::Cfg>> rows;
@@ -176,7 +195,9 @@ int load_table_file(const char *path, std::string *err) {
 }
 
 // The configuration table; on first use it is filled from the file named by
-// the environment variable SQ_TUNE_FILE, if that is set and readable.
+// the environment variable SQ_TUNE_FILE, if that is set, readable and was
+// saved by a library with this build identifier (otherwise the defaults
+// stay).
 ConfigTable &table() {
     static std::once_flag once;
     std::call_once(once, [] {
@@ -271,6 +292,8 @@ const char *sq_last_error(void) { return g_error.c_str(); }
 
 int sq_abi_version(void) { return 100; }
 
+const char *sq_build_id(void) { return SQ_BUILD_ID; }
+
 int sq_debug_fail_next(const char *entry_point) {
     g_fail_next = entry_point ? entry_point : "";
     return ok();
@@ -314,6 +337,25 @@ int sq_uniform2_f32(uint64_t key, uint64_t ctr_base, size_t n, float *out, sq_st
 
 int sq_uniform_f64(uint64_t key, uint64_t ctr_base, size_t n, double *out, sq_stream_t stream) {
     return plain_entry(SQ_KERNEL_UNIFORM_F64, key, ctr_base, n, out, 8, stream, "sq_uniform_f64");
+}
+
+int sq_fill_u32(uint32_t value, size_t n, uint32_t *out, const sq_launch_config *cfg,
+                sq_stream_t stream) {
+    if (n == 0) return ok();
+    if (out == nullptr) return fail(SQ_EINVAL, "sq_fill_u32: out is NULL with n = %zu", n);
+    if (!aligned(out, 4)) return fail(SQ_EINVAL, "sq_fill_u32: out is not 4-byte aligned");
+    if (n > kMaxElems) return fail(SQ_ERANGE, "sq_fill_u32: n = %zu exceeds 2^62", n);
+    sq::Cfg c = table().get(SQ_KERNEL_U32, n);
+    if (cfg) {
+        c = sq::Cfg{cfg->variant, cfg->block, cfg->ctas_per_sm};
+        if (!valid_cfg(SQ_KERNEL_U32, c))
+            return fail(SQ_EINVAL, "sq_fill_u32: invalid configuration (variant %d, block %d, ctas %d)",
+                        c.variant, c.block, c.ctas_per_sm);
+    }
+    if (injected("sq_fill_u32")) return injected_fail("sq_fill_u32");
+    const cudaError_t e = sq::launch_plain(sq::kFillKernelId, c, value, 0, n, out, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "sq_fill_u32");
+    return ok();
 }
 
 static int strided_entry(bool wide, uint64_t key, uint64_t base, uint64_t stride, size_t n, void *out,
@@ -366,7 +408,7 @@ int sq_batch(const uint64_t *keys, const uint64_t *ctr_bases, const int64_t *len
     const int rc = batch_checks(keys, ctr_bases, lengths, offsets, nstreams, out, "sq_batch");
     if (rc != SQ_OK) return rc;
     if (injected("sq_batch")) return injected_fail("sq_batch");
-    const sq::Cfg cfg = table().get(SQ_KERNEL_BATCH, 0);
+    const sq::Cfg cfg = table().get(SQ_KERNEL_BATCH, nstreams);
     const cudaError_t e = sq::launch_batch(cfg, keys, ctr_bases, lengths, offsets, nstreams, out,
                                            static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "sq_batch");
@@ -601,7 +643,9 @@ int sq_autotune(int kernel_id, size_t n_hint) {
             best_cfg = c;
         }
     }
-    table().set(kernel_id, n_hint, best_cfg);
+    // The batch table is indexed by stream count; the synthetic 64-stream
+    // pick (tile variants only) becomes the default for every count.
+    table().set(kernel_id, kernel_id == SQ_KERNEL_BATCH ? 0 : n_hint, best_cfg);
     return ok();
 }
 
@@ -633,7 +677,7 @@ int sq_autotune_batch(const uint64_t *keys, const uint64_t *ctr_bases, const int
     const double extent = static_cast<double>(last_off) + static_cast<double>(last_len);
     const bool short_streams = extent > 0 && extent / static_cast<double>(nstreams) <= 8192.0;
     float best = 1e30f;
-    sq::Cfg best_cfg = table().get(SQ_KERNEL_BATCH, 0);
+    sq::Cfg best_cfg = table().get(SQ_KERNEL_BATCH, nstreams);
     const int blocks[4] = {64, 128, 256, 512};
     const int ctas_opts[4] = {1, 2, 4, 0};
     const int nv = short_streams ? sq::batch_num_variants() : 4;
@@ -670,7 +714,7 @@ int sq_autotune_batch(const uint64_t *keys, const uint64_t *ctr_bases, const int
     }
     cudaStreamDestroy(st);
     if (e != cudaSuccess) return cuda_fail(e, "sq_autotune_batch: candidate launch");
-    table().set(SQ_KERNEL_BATCH, 0, best_cfg);
+    table().set(SQ_KERNEL_BATCH, nstreams, best_cfg);
     return ok();
 }
 
@@ -679,7 +723,7 @@ int sq_autotune_save(const char *path) {
     const std::string name = device_name();
     FILE *f = fopen(path, "w");
     if (!f) return fail(SQ_EINVAL, "sq_autotune_save: cannot open %s", path);
-    fprintf(f, "squares-autotune 1\ndevice %s\n", name.c_str());
+    fprintf(f, "squares-autotune 2\ndevice %s\ncode %s\n", name.c_str(), SQ_BUILD_ID);
     ConfigTable &t = table();
     {
         std::lock_guard<std::mutex> g(t.m);
@@ -723,8 +767,8 @@ int sq_batch_graph_create(const uint64_t *keys, const uint64_t *ctr_bases, const
     sq_graph_s *g = new sq_graph_s;
     e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        const cudaError_t le = sq::launch_batch(table().get(SQ_KERNEL_BATCH, 0), keys, ctr_bases, lengths,
-                                                offsets, nstreams, out, st);
+        const cudaError_t le = sq::launch_batch(table().get(SQ_KERNEL_BATCH, nstreams), keys, ctr_bases,
+                                                lengths, offsets, nstreams, out, st);
         e = cudaStreamEndCapture(st, &g->graph);
         if (le != cudaSuccess) e = le;
     }

@@ -31,7 +31,10 @@ bool in_device_memory(const void *p);
 
 // --- plain generators (sq_u32, sq_u64, uniform, bf16, normal) -------------
 // kernel_id is one of SQ_KERNEL_U32, _U64, _UNIFORM_F32, _UNIFORM_BF16,
-// _NORMAL_F32, _UNIFORM2_F32, _UNIFORM_F64. `out` is the caller's buffer; element type per kernel.
+// _NORMAL_F32, _UNIFORM2_F32, _UNIFORM_F64, or kFillKernelId (the
+// write-only store-ceiling kernel: uint32 elements, all equal to the low 32
+// bits of `key`). `out` is the caller's buffer; element type per kernel.
+constexpr int kFillKernelId = 100;
 int plain_num_variants();
 const char *plain_variant_name(int variant);
 cudaError_t launch_plain(int kernel_id, const Cfg &cfg, uint64_t key, uint64_t ctr_base,

@@ -43,6 +43,7 @@ __device__ __forceinline__ void walk(uint64_t y, uint64_t e, uint64_t key, uint6
 // EPC = output elements per counter.
 
 struct OpU32 {
+    static constexpr int kHeadParity = 0;
     using T = uint32_t;
     static constexpr int EPC = 1;
     template <int W>
@@ -57,6 +58,7 @@ struct OpU32 {
 };
 
 struct OpU64 {
+    static constexpr int kHeadParity = 0;
     using T = uint64_t;
     static constexpr int EPC = 1;
     template <int W>
@@ -73,6 +75,7 @@ struct OpU64 {
 };
 
 struct OpUniformF32 {
+    static constexpr int kHeadParity = 0;
     using T = float;
     static constexpr int EPC = 1;
     template <int W>
@@ -87,6 +90,7 @@ struct OpUniformF32 {
 };
 
 struct OpUniformBF16 {
+    static constexpr int kHeadParity = 0;
     using T = uint16_t;
     static constexpr int EPC = 1;
     template <int W>
@@ -104,15 +108,21 @@ struct OpUniformBF16 {
 };
 
 struct OpNormalF32 {
+    static constexpr int kHeadParity = 0;
     using T = float;
     static constexpr int EPC = 2;
+    // the two elements of one counter
+    __device__ static uint2 pair(uint64_t t, uint64_t y, uint64_t z) {
+        const uint64_t v = squares64_tyz(t, y, z);
+        const float2 n = box_muller(hi32(v), lo32(v));
+        return make_uint2(__float_as_uint(n.x), __float_as_uint(n.y));
+    }
     template <int W>
     __device__ static void chunk(uint64_t y, uint64_t e, uint64_t key, uint64_t c2, uint32_t (&w)[W]) {
         walk<W / 2>(y, e, key, c2, [&](int j, uint64_t t, uint64_t yy, uint64_t z) {
-            const uint64_t v = squares64_tyz(t, yy, z);
-            const float2 n = box_muller(hi32(v), lo32(v));
-            w[2 * j] = __float_as_uint(n.x);
-            w[2 * j + 1] = __float_as_uint(n.y);
+            const uint2 v = pair(t, yy, z);
+            w[2 * j] = v.x;
+            w[2 * j + 1] = v.y;
         });
     }
     __device__ static T single(uint64_t ctr0, uint64_t key, uint64_t e) {
@@ -125,14 +135,19 @@ struct OpNormalF32 {
 // Two floats per squares64 output: the upper 32 bits, then the lower
 // (Section 5's split into halves), each as floor(half / 2^8) * 2^-24.
 struct OpUniform2F32 {
+    static constexpr int kHeadParity = 0;
     using T = float;
     static constexpr int EPC = 2;
+    __device__ static uint2 pair(uint64_t t, uint64_t y, uint64_t z) {
+        const uint64_t v = squares64_tyz(t, y, z);
+        return make_uint2(__float_as_uint(uniform24(hi32(v))), __float_as_uint(uniform24(lo32(v))));
+    }
     template <int W>
     __device__ static void chunk(uint64_t y, uint64_t e, uint64_t key, uint64_t c2, uint32_t (&w)[W]) {
         walk<W / 2>(y, e, key, c2, [&](int j, uint64_t t, uint64_t yy, uint64_t z) {
-            const uint64_t v = squares64_tyz(t, yy, z);
-            w[2 * j] = __float_as_uint(uniform24(hi32(v)));
-            w[2 * j + 1] = __float_as_uint(uniform24(lo32(v)));
+            const uint2 v = pair(t, yy, z);
+            w[2 * j] = v.x;
+            w[2 * j + 1] = v.y;
         });
     }
     __device__ static T single(uint64_t ctr0, uint64_t key, uint64_t e) {
@@ -141,9 +156,47 @@ struct OpUniform2F32 {
     }
 };
 
+// A two-elements-per-counter op whose chunks start at the second element of
+// a counter's pair: an output pointer that is 4-byte but not 8-byte aligned
+// puts the 16- and 32-byte boundaries at odd element indices. A chunk of W
+// elements then spans W/2 + 1 counters: the first contributes its second
+// element, the last its first, so each chunk computes one pair more than it
+// stores (W/2 + 1 for W/2), and the vector stores stay aligned.
+template <class Op>
+struct OddPairs {
+    static constexpr int kHeadParity = 1;
+    using T = typename Op::T;
+    static constexpr int EPC = 2;
+    template <int W>
+    __device__ static void chunk(uint64_t y, uint64_t e, uint64_t key, uint64_t c2, uint32_t (&w)[W]) {
+        walk<W / 2 + 1>(y, e, key, c2, [&](int j, uint64_t t, uint64_t yy, uint64_t z) {
+            const uint2 v = Op::pair(t, yy, z);
+            if (j > 0) w[2 * j - 1] = v.x;
+            if (j < W / 2) w[2 * j] = v.y;
+        });
+    }
+    __device__ static T single(uint64_t ctr0, uint64_t key, uint64_t e) { return Op::single(ctr0, key, e); }
+};
+
+// Store ceiling: the plain kernels' chunking, grid and store path with no
+// generator arithmetic; every element is the 32-bit value passed in place
+// of the key.
+struct OpFill {
+    static constexpr int kHeadParity = 0;
+    using T = uint32_t;
+    static constexpr int EPC = 1;
+    template <int W>
+    __device__ static void chunk(uint64_t, uint64_t, uint64_t key, uint64_t, uint32_t (&w)[W]) {
+#pragma unroll
+        for (int j = 0; j < W; ++j) w[j] = static_cast<uint32_t>(key);
+    }
+    __device__ static T single(uint64_t, uint64_t key, uint64_t) { return static_cast<uint32_t>(key); }
+};
+
 // 53-bit double uniforms floor(squares64 / 2^11) * 2^-53, built with
 // integer operations only (see uniform53_bits).
 struct OpUniformF64 {
+    static constexpr int kHeadParity = 0;
     using T = double;
     static constexpr int EPC = 1;
     template <int W>
@@ -324,6 +377,7 @@ const void *plain_fn_for(int kernel_id, int variant) {
         case SQ_KERNEL_NORMAL_F32: return plain_fn<OpNormalF32>(variant);
         case SQ_KERNEL_UNIFORM2_F32: return plain_fn<OpUniform2F32>(variant);
         case SQ_KERNEL_UNIFORM_F64: return plain_fn<OpUniformF64>(variant);
+        case kFillKernelId: return plain_fn<OpFill>(variant);
         default: return nullptr;
     }
 }
@@ -338,7 +392,7 @@ cudaError_t launch_bulk(const Cfg &cfg, uint64_t key, uint64_t ctr0, size_t n, v
     const uintptr_t addr = reinterpret_cast<uintptr_t>(out);
     size_t head = ((32 - (addr % 32)) % 32) / sizeof(T);
     if (head > n) head = n;
-    if (head % Op::EPC != 0) head = n;
+    if (head % Op::EPC != Op::kHeadParity) head = n;  // chunk form of the other parity: all singles
     const size_t nwc = (n - head) / wc_elems;
     const int ctas = cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : max_ctas;
     uint64_t grid = static_cast<uint64_t>(current_sm_count()) * (ctas > 0 ? ctas : 1);
@@ -363,7 +417,7 @@ cudaError_t launch_op(const Cfg &cfg, uint64_t key, uint64_t ctr0, size_t n, voi
     const uintptr_t addr = reinterpret_cast<uintptr_t>(out);
     size_t head = ((align - (addr % align)) % align) / sizeof(T);
     if (head > n) head = n;
-    if (head % Op::EPC != 0) head = n;  // pairs would straddle chunks: all singles
+    if (head % Op::EPC != Op::kHeadParity) head = n;  // chunk form of the other parity: all singles
     const size_t nvec = (n - head) / epv;
     const int ctas = cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : max_ctas;
     uint64_t grid = static_cast<uint64_t>(current_sm_count()) * (ctas > 0 ? ctas : 1);
@@ -382,6 +436,39 @@ cudaError_t launch_op(const Cfg &cfg, uint64_t key, uint64_t ctr0, size_t n, voi
         default: plain_kernel<Op, 64, true><<<grid, cfg.block, 0, stream>>>(key, ctr0, o, n, head, nvec); break;
     }
     return cudaGetLastError();
+}
+
+// Elements before the first aligned chunk for a variant: the bulk body and
+// the 32- and 64-byte bodies start at a 32-byte boundary, the 16-byte ones at
+// a 16-byte boundary.
+size_t head_elems(int variant, const void *out, size_t elem, size_t n) {
+    const size_t align = variant == kBulkVariant ? 32 : (variant_bytes(variant) > 32 ? 32 : variant_bytes(variant));
+    const size_t head = ((align - (reinterpret_cast<uintptr_t>(out) % align)) % align) / elem;
+    return head > n ? n : head;
+}
+
+template <class Op>
+cudaError_t launch_kind(const Cfg &c, uint64_t key, uint64_t ctr_base, size_t n, void *out,
+                        cudaStream_t stream) {
+    if constexpr (Op::EPC == 2) {
+        // An odd head (a 4-byte but not 8-byte aligned float pointer) takes
+        // the chunk form that starts mid-pair.
+        if (head_elems(c.variant, out, sizeof(typename Op::T), n) % 2 == 1) {
+            using Odd = OddPairs<Op>;
+            if (c.variant == kBulkVariant) prepare_bulk<Odd>();
+            const int max_ctas = c.ctas_per_sm > 0
+                                     ? c.ctas_per_sm
+                                     : occupancy(plain_fn<Odd>(c.variant), c.block,
+                                                 c.variant == kBulkVariant ? bulk_smem(c.block) : 0);
+            return launch_op<Odd>(c, key, ctr_base, n, out, stream, max_ctas);
+        }
+    }
+    if (c.variant == kBulkVariant) prepare_bulk<Op>();
+    const int max_ctas = c.ctas_per_sm > 0
+                             ? c.ctas_per_sm
+                             : occupancy(plain_fn<Op>(c.variant), c.block,
+                                         c.variant == kBulkVariant ? bulk_smem(c.block) : 0);
+    return launch_op<Op>(c, key, ctr_base, n, out, stream, max_ctas);
 }
 
 }  // namespace
@@ -414,21 +501,15 @@ cudaError_t launch_plain(int kernel_id, const Cfg &cfg, uint64_t key, uint64_t c
     // 128 B line half written per store, which halves the link's write rate,
     // and the bulk copy stages for device memory only.
     if (variant_bytes(c.variant) > 32 && !in_device_memory(out)) c.variant = c.variant == 5 ? 1 : 0;
-    const int max_ctas = c.ctas_per_sm > 0 ? c.ctas_per_sm
-                                           : plain_max_ctas_per_sm(kernel_id, c.variant, c.block);
     switch (kernel_id) {
-        case SQ_KERNEL_U32: return launch_op<OpU32>(c, key, ctr_base, n, out, stream, max_ctas);
-        case SQ_KERNEL_U64: return launch_op<OpU64>(c, key, ctr_base, n, out, stream, max_ctas);
-        case SQ_KERNEL_UNIFORM_F32:
-            return launch_op<OpUniformF32>(c, key, ctr_base, n, out, stream, max_ctas);
-        case SQ_KERNEL_UNIFORM_BF16:
-            return launch_op<OpUniformBF16>(c, key, ctr_base, n, out, stream, max_ctas);
-        case SQ_KERNEL_NORMAL_F32:
-            return launch_op<OpNormalF32>(c, key, ctr_base, n, out, stream, max_ctas);
-        case SQ_KERNEL_UNIFORM2_F32:
-            return launch_op<OpUniform2F32>(c, key, ctr_base, n, out, stream, max_ctas);
-        case SQ_KERNEL_UNIFORM_F64:
-            return launch_op<OpUniformF64>(c, key, ctr_base, n, out, stream, max_ctas);
+        case SQ_KERNEL_U32: return launch_kind<OpU32>(c, key, ctr_base, n, out, stream);
+        case SQ_KERNEL_U64: return launch_kind<OpU64>(c, key, ctr_base, n, out, stream);
+        case SQ_KERNEL_UNIFORM_F32: return launch_kind<OpUniformF32>(c, key, ctr_base, n, out, stream);
+        case SQ_KERNEL_UNIFORM_BF16: return launch_kind<OpUniformBF16>(c, key, ctr_base, n, out, stream);
+        case SQ_KERNEL_NORMAL_F32: return launch_kind<OpNormalF32>(c, key, ctr_base, n, out, stream);
+        case SQ_KERNEL_UNIFORM2_F32: return launch_kind<OpUniform2F32>(c, key, ctr_base, n, out, stream);
+        case SQ_KERNEL_UNIFORM_F64: return launch_kind<OpUniformF64>(c, key, ctr_base, n, out, stream);
+        case kFillKernelId: return launch_kind<OpFill>(c, key, ctr_base, n, out, stream);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -94,6 +94,29 @@ def test_strided_and_keys_argument_checks(lib):
         assert e.value.status == sq.SQ_EINVAL
 
 
+def test_fill_argument_checks(lib):
+    """The store-ceiling kernel's entry point checks its arguments on the
+    host like the generators: n = 0 is a no-op, NULL or misaligned output
+    and invalid launch configurations are refused before any CUDA call."""
+    sq.sq_fill_u32(7, 0, 0)
+    with pytest.raises(sq.SquaresError) as e:
+        sq.sq_fill_u32(7, 10, 0)
+    assert e.value.status == sq.SQ_EINVAL
+    with pytest.raises(sq.SquaresError) as e:
+        sq.sq_fill_u32(7, 10, 0x1002)
+    assert e.value.status == sq.SQ_EINVAL
+    with pytest.raises(sq.SquaresError) as e:
+        sq.sq_fill_u32(7, 10, 0x1000, (0, 100, 0))
+    assert e.value.status == sq.SQ_EINVAL and "configuration" in e.value.message
+    with pytest.raises(sq.SquaresError) as e:
+        sq.sq_fill_u32(7, (1 << 62) + 1, 0x1000)
+    assert e.value.status == sq.SQ_ERANGE
+    sq.sq_debug_fail_next("sq_fill_u32")
+    with pytest.raises(sq.SquaresError) as e:
+        sq.sq_fill_u32(7, 16, 0x1000, (1, 256, 0))
+    assert e.value.status == sq.SQ_ECUDA and "injected" in e.value.message
+
+
 def test_batch_and_fused_argument_checks(lib):
     sq.sq_batch(0, 0, 0, 0, 0, 0)  # empty batch
     with pytest.raises(sq.SquaresError) as e:
@@ -142,6 +165,12 @@ def test_config_table(lib):
     sq.sq_set_config(sq.SQ_KERNEL_BATCH, 0, 1, 64, 0)
     assert sq.sq_get_config(sq.SQ_KERNEL_BATCH, 0).block == 64
     sq.sq_set_config(sq.SQ_KERNEL_BATCH, 0, 0, 256, 0)
+    # the batch table is keyed by stream count: a pick for a batch of 2^20
+    # short streams leaves batches of a few thousand long ones alone
+    sq.sq_set_config(sq.SQ_KERNEL_BATCH, 1 << 20, 9, 512, 0)
+    assert sq.sq_get_config(sq.SQ_KERNEL_BATCH, (1 << 20) + 100).variant == 9
+    assert sq.sq_get_config(sq.SQ_KERNEL_BATCH, 4096).variant == 0
+    sq.sq_set_config(sq.SQ_KERNEL_BATCH, 0, 0, 256, 0)
     with pytest.raises(sq.SquaresError):
         sq.sq_get_config(42, 0)
     with pytest.raises(sq.SquaresError):
@@ -155,6 +184,81 @@ def test_autotune_file_errors(lib, tmp_path):
     bad.write_text("not a tune file\n")
     with pytest.raises(sq.SquaresError):
         sq.sq_autotune_load(str(bad))
+
+
+def _device_name():
+    import torch
+
+    return torch.cuda.get_device_name(0) if torch.cuda.is_available() else "unknown"
+
+
+def test_build_id_is_the_kernel_code_hash(lib):
+    """The library reports the hash of the kernel sources' code it was built
+    from (the identifier a tuned table is keyed by)."""
+    from paper_2004_06278_gb300 import build as libbuild
+
+    bid = sq.sq_build_id()
+    assert len(bid) == 16 and int(bid, 16) >= 0
+    assert bid == libbuild.build_id()
+
+
+def test_tuned_table_from_other_kernel_code_is_ignored(lib, tmp_path):
+    """A table saved by a library built from other kernel code is not
+    applied: the load fails with a message naming both code identifiers and
+    the table keeps its entries. A file of format 1 (no code identifier) is
+    refused the same way; the same rows under this library's identifier are
+    applied."""
+    dev = _device_name()
+    rows = "0 20 4 512 2\n"
+    sq.sq_set_config(sq.SQ_KERNEL_U32, 0, 0, 256, 0)
+    try:
+        other = tmp_path / "other_code.txt"
+        other.write_text(f"squares-autotune 2\ndevice {dev}\ncode 0123456789abcdef\n{rows}")
+        with pytest.raises(sq.SquaresError) as e:
+            sq.sq_autotune_load(str(other))
+        assert e.value.status == sq.SQ_EINVAL
+        assert "0123456789abcdef" in e.value.message and sq.sq_build_id() in e.value.message
+        assert "0123456789abcdef" in sq.sq_last_error()
+        c = sq.sq_get_config(sq.SQ_KERNEL_U32, 1 << 20)
+        assert (c.variant, c.block, c.ctas_per_sm) == (0, 256, 0)
+        old = tmp_path / "format1.txt"
+        old.write_text(f"squares-autotune 1\ndevice {dev}\n{rows}")
+        with pytest.raises(sq.SquaresError) as e:
+            sq.sq_autotune_load(str(old))
+        assert "none" in e.value.message
+        assert sq.sq_get_config(sq.SQ_KERNEL_U32, 1 << 20).variant == 0
+        good = tmp_path / "this_code.txt"
+        good.write_text(f"squares-autotune 2\ndevice {dev}\ncode {sq.sq_build_id()}\n{rows}")
+        sq.sq_autotune_load(str(good))
+        c = sq.sq_get_config(sq.SQ_KERNEL_U32, 1 << 20)
+        assert (c.variant, c.block, c.ctas_per_sm) == (4, 512, 2)
+    finally:
+        sq.sq_set_config(sq.SQ_KERNEL_U32, 0, 0, 256, 0)
+
+
+def test_autotune_save_round_trip(lib, tmp_path):
+    """sq_autotune_save writes format 2 with the device name and the build
+    identifier; loading it back restores every entry."""
+    sq.sq_set_config(sq.SQ_KERNEL_U64, 1 << 24, 5, 512, 1)
+    sq.sq_set_config(sq.SQ_KERNEL_BATCH, 1 << 20, 9, 512, 0)
+    try:
+        path = tmp_path / "saved.txt"
+        sq.sq_autotune_save(str(path))
+        lines = path.read_text().splitlines()
+        assert lines[0] == "squares-autotune 2"
+        assert lines[1] == f"device {_device_name()}"
+        assert lines[2] == f"code {sq.sq_build_id()}"
+        sq.sq_set_config(sq.SQ_KERNEL_U64, 0, 0, 256, 0)
+        sq.sq_set_config(sq.SQ_KERNEL_BATCH, 0, 0, 256, 0)
+        sq.sq_autotune_load(str(path))
+        c = sq.sq_get_config(sq.SQ_KERNEL_U64, 1 << 24)
+        assert (c.variant, c.block, c.ctas_per_sm) == (5, 512, 1)
+        b = sq.sq_get_config(sq.SQ_KERNEL_BATCH, (1 << 20) + 7)
+        assert (b.variant, b.block) == (9, 512)
+        assert sq.sq_get_config(sq.SQ_KERNEL_BATCH, 4096).variant == 0
+    finally:
+        sq.sq_set_config(sq.SQ_KERNEL_U64, 0, 0, 256, 0)
+        sq.sq_set_config(sq.SQ_KERNEL_BATCH, 0, 0, 256, 0)
 
 
 def test_last_error_is_per_call(lib):
@@ -190,20 +294,24 @@ def test_injected_launch_failure_reaches_the_caller(lib):
 
 def test_tune_file_from_environment(lib, tmp_path):
     """SQ_TUNE_FILE: the table is loaded from that file on first use (checked
-    in a fresh process; entries for another device name are ignored)."""
+    in a fresh process; a table for another device name, or saved by a
+    library built from other kernel code, is ignored)."""
     import subprocess
     import sys
 
     import torch
 
     name = torch.cuda.get_device_name(0) if torch.cuda.is_available() else "unknown"
+    bid = sq.sq_build_id()
     good = tmp_path / "tune.txt"
-    good.write_text(f"squares-autotune 1\ndevice {name}\n0 20 4 512 2\n")
+    good.write_text(f"squares-autotune 2\ndevice {name}\ncode {bid}\n0 20 4 512 2\n")
     other = tmp_path / "other.txt"
-    other.write_text("squares-autotune 1\ndevice some other GPU\n0 20 4 512 2\n")
+    other.write_text(f"squares-autotune 2\ndevice some other GPU\ncode {bid}\n0 20 4 512 2\n")
+    stale = tmp_path / "stale.txt"
+    stale.write_text(f"squares-autotune 2\ndevice {name}\ncode ffffffffffffffff\n0 20 4 512 2\n")
     code = ("import paper_2004_06278_gb300 as sq; c = sq.sq_get_config(0, 1 << 20); "
             "print(c.variant, c.block, c.ctas_per_sm)")
-    for path, want in ((good, "4 512 2"), (other, "0 256 0")):
+    for path, want in ((good, "4 512 2"), (other, "0 256 0"), (stale, "0 256 0")):
         env = dict(os.environ, SQ_TUNE_FILE=str(path))
         r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT,
                            env=env, timeout=120)

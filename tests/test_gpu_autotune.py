@@ -44,7 +44,7 @@ def test_autotune_batch_on_own_arrays(gpu_lib):
     try:
         C.sq_autotune_batch(keys.data_ptr(), bases.data_ptr(), lengths.data_ptr(),
                             offsets.data_ptr(), b.nstreams, out.data_ptr())
-        cfg = C.sq_get_config(C.SQ_KERNEL_BATCH, 0)
+        cfg = C.sq_get_config(C.SQ_KERNEL_BATCH, b.nstreams)
         assert 0 <= cfg.variant < C.sq_num_variants(C.SQ_KERNEL_BATCH)
         want = np.full(b.total + 9, fill, dtype=np.uint32)
         oracle.batch32(oracle.make_keys(b.key_seed, b.nstreams), b.bases, b.lengths, b.offsets, want)
@@ -71,7 +71,7 @@ def test_autotune_batch_long_streams_keeps_tile_variants(gpu_lib):
     try:
         C.sq_autotune_batch(keys.data_ptr(), bases.data_ptr(), lengths.data_ptr(),
                             offsets.data_ptr(), b.nstreams, out.data_ptr())
-        cfg = C.sq_get_config(C.SQ_KERNEL_BATCH, 0)
+        cfg = C.sq_get_config(C.SQ_KERNEL_BATCH, b.nstreams)
         assert 0 <= cfg.variant < 4, C.sq_variant_name(C.SQ_KERNEL_BATCH, cfg.variant)
         want = np.full(b.total + 5, fill, dtype=np.uint32)
         oracle.batch32(oracle.make_keys(b.key_seed, b.nstreams), b.bases, b.lengths, b.offsets, want)

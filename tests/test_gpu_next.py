@@ -109,6 +109,7 @@ def test_new_variants_every_config(gpu_lib):
             C.sq_set_config(C.SQ_KERNEL_UNIFORM2_F32, 0, v, 256, 0)
             C.sq_set_config(C.SQ_KERNEL_UNIFORM_F64, 0, v, 512, 0)
             assert np.array_equal(_run(C.sq_uniform2_f32, 4, np.float32, key, 5, n=n, off=2).view(np.uint32), w2)
+            assert np.array_equal(_run(C.sq_uniform2_f32, 4, np.float32, key, 5, n=n, off=1).view(np.uint32), w2)
             assert np.array_equal(_run(C.sq_uniform_f64, 8, np.float64, key, 5, n=n, off=1).view(np.uint64), w64)
     finally:
         C.sq_set_config(C.SQ_KERNEL_UNIFORM2_F32, 0, 0, 256, 0)

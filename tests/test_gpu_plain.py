@@ -207,3 +207,28 @@ def test_capture_with_wide_and_bulk_variants(gpu_lib, name):
     finally:
         C.sq_set_config(C.SQ_KERNEL_U32, 0, 0, 256, 0)
         C.sq_set_config(C.SQ_KERNEL_U64, 0, 0, 256, 0)
+
+
+def test_fill_store_ceiling_kernel(gpu_lib):
+    """sq_fill_u32 (the write-only kernel the benchmark measures the store
+    ceiling with) writes exactly [out, out + n) with its value in every
+    store variant and block size, at every 4-byte offset, in device memory
+    and in pinned host memory."""
+    import torch
+
+    n = 2 * 152 * 512 * 16 + 13
+    value = 0x9E3779B9
+    for v in range(C.sq_num_variants(C.SQ_KERNEL_U32)):
+        for block in (128, 512):
+            for off in (0, 1, 3, 7):
+                g = Guarded(n * 4, off * 4)
+                C.sq_fill_u32(value, n, g.ptr, (v, block, 0), stream_handle())
+                assert g.guards_intact(), (v, block, off)
+                assert np.all(g.payload(np.uint32) == value), (v, block, off)
+    host = torch.zeros(n + 8, dtype=torch.int32, pin_memory=True)
+    for off in (0, 3):
+        host.zero_()
+        C.sq_fill_u32(value, n, host[off:].data_ptr(), None, stream_handle())
+        torch.cuda.synchronize()
+        got = host.numpy().view(np.uint32)
+        assert np.all(got[off:off + n] == value) and not got[:off].any() and not got[off + n:].any()

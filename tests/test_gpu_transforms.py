@@ -91,6 +91,53 @@ def test_normal_large_sample_error_report(gpu_lib):
     assert ntail > 0
 
 
+def test_odd_offset_pairs_take_the_vector_path(gpu_lib):
+    """A float pointer that is 4-byte but not 8-byte aligned puts every
+    vector boundary in the middle of a counter's pair. The launcher then runs
+    the chunk form that starts at a pair's second element (one pair more per
+    chunk than it stores) instead of writing every element alone: checked by
+    value against the oracle in every store variant, and by time, where the
+    odd offset stays well under the twice-the-work of the per-element path."""
+    import torch
+
+    key = int(gpu_lib.make_keys(14, 1)[0])
+    n = 2 * 152 * 512 * 16 + 9
+    wn = oracle.normal_f64(key, 11, n)
+    w2 = oracle.uniform2_f32(key, 11, n).view(np.uint32)
+    try:
+        for v in range(C.sq_num_variants(C.SQ_KERNEL_NORMAL_F32)):
+            for kid in (C.SQ_KERNEL_NORMAL_F32, C.SQ_KERNEL_UNIFORM2_F32):
+                C.sq_set_config(kid, 0, v, 256, 0)
+            for off in (1, 3):
+                z = _run(C.sq_normal_f32, 4, np.float32, key, 11, n, off)
+                max_abs, max_rel, _ = normal_errors(z, wn)
+                assert max_abs <= ABS_TOL and max_rel <= REL_TOL, (v, off, max_abs, max_rel)
+                got = _run(C.sq_uniform2_f32, 4, np.float32, key, 11, n, off)
+                assert np.array_equal(got.view(np.uint32), w2), (v, off)
+    finally:
+        for kid in (C.SQ_KERNEL_NORMAL_F32, C.SQ_KERNEL_UNIFORM2_F32):
+            C.sq_set_config(kid, 0, 0, 256, 0)
+
+    m = 1 << 26
+    buf = torch.empty(m + 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def ms(ptr):
+        for _ in range(2):
+            C.sq_normal_f32(key, 0, m, ptr, stream_handle())
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(5):
+            C.sq_normal_f32(key, 0, m, ptr, stream_handle())
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 5
+
+    even, odd = ms(buf.data_ptr()), ms(buf.data_ptr() + 4)
+    assert odd < 1.4 * even, (even, odd)
+
+
 def test_transform_variants(gpu_lib):
     key = int(gpu_lib.make_keys(12, 1)[0])
     n = 2 * 152 * 512 * 16 + 5
