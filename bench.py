@@ -255,23 +255,11 @@ def reference_arm(args, rank, world):
 # --------------------------------------------------------------------------
 # our arm
 
-def _code_only(text: str) -> str:
-    """C/C++/CUDA source without comments and whitespace: what the compiler
-    sees, so that edits to comments do not retire a profile."""
-    import re
-
-    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
-    text = re.sub(r"//[^\n]*", " ", text)
-    return re.sub(r"\s+", "", text)
-
-
 def source_hash(*rel):
     """Hash of the kernel sources' code (comments and whitespace removed)."""
-    h = hashlib.sha256()
-    for r in rel:
-        with open(os.path.join(ROOT, r), encoding="utf-8") as f:
-            h.update(_code_only(f.read()).encode())
-    return h.hexdigest()[:16]
+    from paper_2004_06278_gb300 import build as libbuild
+
+    return libbuild.code_hash([os.path.join(ROOT, r) for r in rel])
 
 
 KERNEL_SOURCES = ("paper_2004_06278_gb300/csrc/kernels_plain.cu",
@@ -340,8 +328,12 @@ def run_ours(args, rank, world, local):
     out32 = torch.empty(N32, dtype=torch.int32, device=dev)
     tuned_from_file = bool(args.tune_file and os.path.exists(args.tune_file))
     if tuned_from_file:
-        C.sq_autotune_load(args.tune_file)
-    elif not args.no_tune:
+        try:
+            C.sq_autotune_load(args.tune_file)
+        except C.SquaresError as e:  # tuned on other kernel code: tune again
+            print(f"bench: {e}; tuning again", file=sys.stderr)
+            tuned_from_file = False
+    if not tuned_from_file and not args.no_tune:
         C.sq_autotune(C.SQ_KERNEL_U64, N64)
         C.sq_autotune(C.SQ_KERNEL_U32, N32)
     cfg32 = C.sq_get_config(C.SQ_KERNEL_U32, N32)
@@ -400,26 +392,38 @@ def run_ours(args, rank, world, local):
         r_hbm32 = hbm * 1e9 / 4
         r_int32 = lane_cycles / HEAVY_CYCLES_SQ32
         r_int64 = lane_cycles / HEAVY_CYCLES_SQ64
-        if r_int32 < r_hbm32:
-            roof = {"bound": "alu", "achieved": r32 / 1e9, "peak": r_int32 / 1e9,
-                    "unit": "Gsamples/s", "frac": r32 / r_int32}
-        else:
-            roof = {"bound": "hbm", "achieved": r32 * 4 / 1e9, "peak": hbm, "unit": "GB/s",
-                    "frac": r32 / r_hbm32}
+        store = store_ceiling(torch, C, out32, N32, stream)
+        store_gbs = store["GBps"]
+        # Bound from the counters: the squares32 kernel runs as fast without
+        # its stores as with them and its FMA-heavy pipe is the busiest unit
+        # (profiles/sq_u32_plain_2p28.md), so it is bound by integer issue,
+        # not by HBM; the peak is the integer model of the algorithm (three
+        # multiplying rounds, 18 FMA-heavy cycles per warp of samples).
+        roof = {"bound": "alu", "achieved": r32 / 1e9, "peak": r_int32 / 1e9,
+                "unit": "Gsamples/s", "frac": r32 / r_int32}
         roof.update({
             "kernel": "sq_u32 (plain squares32, 2^32 outputs per launch)",
             "traffic": profiled_traffic("sq_u32_plain"),
+            "traffic_unit": "bytes per launch (dram read + write)",
             "algorithmic_bytes": 4 * N32,
             "avg_launch_ms": ms32,
-            "peak_source": f"{peak_src}: hbm {hbm} GB/s (MEASURED_PEAKS.json); integer: "
-                           f"{sms} SMs x {LANES_PER_SM} lanes x {sm_max} MHz / "
+            "peak_source": f"integer model: {sms} SMs x {LANES_PER_SM} lanes x {sm_max} MHz / "
                            f"{HEAVY_CYCLES_SQ32} FMA-heavy cycles per warp-sample = "
-                           f"{r_int32 / 1e9:.0f} Gsamples/s",
+                           f"{r_int32 / 1e9:.0f} Gsamples/s; hbm copy {hbm} GB/s ({peak_src}, "
+                           f"MEASURED_PEAKS.json); store-only ceiling measured here with "
+                           f"sq_fill_u32 (best of {store['configs']} launch configurations)",
+            "limiter": "FMA-heavy pipe (ncu: busiest unit; the kernel without stores takes the "
+                       "same time as with them)",
+            "achieved_GBps": r32 * 4 / 1e9,
             "frac_hbm": (r32 * 4 / 1e9) / hbm,
+            "peak_store_only": store_gbs,
+            "frac_store_only": (r32 * 4 / 1e9) / store_gbs,
+            "store_only_config": store["best"],
             "frac_int": r32 / r_int32,
             "squares64": {"avg_launch_ms": ms64, "Gsamples_per_s": r64 / 1e9,
-                          "GBps": r64 * 8 / 1e9, "bound": "hbm" if hbm * 1e9 / 8 < r_int64 else "alu",
-                          "frac_hbm": (r64 * 8 / 1e9) / hbm, "frac_int": r64 / r_int64},
+                          "GBps": r64 * 8 / 1e9, "bound": "hbm" if store_gbs * 1e9 / 8 < r_int64 else "alu",
+                          "frac_hbm": (r64 * 8 / 1e9) / hbm, "frac_store_only": (r64 * 8 / 1e9) / store_gbs,
+                          "frac_int": r64 / r_int64},
         })
         result = {
             "metric": METRIC, "value": value, "unit": "Gsamples/s", "n_gpus": world,
@@ -445,7 +449,8 @@ def run_ours(args, rank, world, local):
     if rank == 0 and not args.no_e2e:
         result["e2e"] = e2e_block(torch, C, key, base64, base32, dev, args.e2e_steps)
     if rank == 0 and not args.no_extras:
-        result["breakdown"] = breakdown(torch, sq, C, workloads, dev, ms32, tuned_from_file)
+        result["breakdown"] = breakdown(torch, sq, C, workloads, dev, ms32, tuned_from_file,
+                                        with_oracle=world == 1 and not args.no_cpu_baseline)
     if rank == 0 and args.tune_file and not tuned_from_file:
         C.sq_autotune_save(args.tune_file)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -458,6 +463,33 @@ def run_ours(args, rank, world, local):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def store_ceiling(torch, C, buf, n, stream, reps=3):
+    """Write-only ceiling of HBM for the generators' store path: sq_fill_u32
+    (their chunking, grid and store variants, no arithmetic) over n uint32
+    elements of `buf`, in every store variant, block size and CTA count the
+    plain kernels use; CUDA events on `stream`. Returns the best rate (GB/s
+    written), its configuration and how many were timed."""
+    sh = int(stream.cuda_stream)
+    best, best_cfg, count = 0.0, None, 0
+    for v in range(C.sq_num_variants(C.SQ_KERNEL_U32)):
+        for block in (128, 256, 512):
+            for ctas in (1, 2, 4, 0):
+                cfg = (v, block, ctas)
+                C.sq_fill_u32(0x5A5A5A5A, n, buf.data_ptr(), cfg, sh)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for _ in range(reps):
+                    C.sq_fill_u32(0x5A5A5A5A, n, buf.data_ptr(), cfg, sh)
+                b.record(stream)
+                torch.cuda.synchronize()
+                gbs = n * 4 * reps / (a.elapsed_time(b) / 1e3) / 1e9
+                count += 1
+                if gbs > best:
+                    best, best_cfg = gbs, [C.sq_variant_name(C.SQ_KERNEL_U32, v), block, ctas]
+    return {"GBps": best, "best": best_cfg, "configs": count}
 
 
 def e2e_block(torch, C, key, base64, base32, dev, steps):
@@ -515,21 +547,49 @@ def e2e_block(torch, C, key, base64, base32, dev, steps):
             host64.view(torch.uint8)[:chunk * 8].copy_(stage[0], non_blocking=True)
         streams[0].synchronize()
 
+    # Host-link probes into the same pinned memory: several copies at once
+    # (one per stream, separate staging buffers and host ranges), and the SMs
+    # storing straight across the link (sq_fill_u32, no arithmetic).
+    link_streams = [torch.cuda.Stream(dev) for _ in range(4)]
+    link_stage = stage + [torch.empty(chunk * 8, dtype=torch.uint8, device=dev) for _ in range(2)]
+    host_bytes = host32.view(torch.uint8)
+
+    def run_copies(k):
+        def run():
+            for i in range(k):
+                with torch.cuda.stream(link_streams[i]):
+                    host_bytes[i * chunk * 8:(i + 1) * chunk * 8].copy_(link_stage[i], non_blocking=True)
+            for st in link_streams[:k]:
+                st.synchronize()
+        return run
+
+    def run_fill():
+        C.sq_fill_u32(0x5A5A5A5A, N32, host32.data_ptr(), None, int(streams[0].cuda_stream))
+        streams[0].synchronize()
+
     dt_copy = timed(run_copy)
     dt_direct = timed(run_direct)
     dt_link = timed(run_link)
+    probes = {"copy_x1_GBps": chunk * 8 / dt_link / 1e9}
+    for k in (2, 4):
+        probes[f"copies_x{k}_GBps"] = k * chunk * 8 / timed(run_copies(k)) / 1e9
+    probes["sm_stores_GBps"] = 4 * N32 / timed(run_fill) / 1e9
+    link = max(probes.values())
     d2h = 8 * N64 + 4 * N32
     best = min(dt_copy, dt_direct)
     res = {"value": (N64 + N32) / best / 1e9, "unit": "Gsamples/s", "h2d_bytes_per_step": 0,
            "d2h_bytes_per_step": d2h, "ms_per_step": best * 1000, "steps": steps,
-           "d2h_GBps": d2h / best / 1e9, "copy_engine_GBps": chunk * 8 / dt_link / 1e9,
-           "frac_of_copy_engine": (d2h / best) / (chunk * 8 / dt_link),
-           "note": "copy_engine_GBps: one 2 GiB cudaMemcpyAsync into the same pinned memory; "
-                   "after a process that moved tens of GB through host memory the copy engine "
-                   "can run well below the SMs' direct stores, so the fraction can exceed 1",
+           "d2h_GBps": d2h / best / 1e9, "copy_engine_GBps": probes["copy_x1_GBps"],
+           "frac_of_copy_engine": (d2h / best / 1e9) / probes["copy_x1_GBps"],
+           "link_ceiling_GBps": link, "frac_of_link": (d2h / best / 1e9) / link,
+           "link_probes": probes,
+           "note": "link_ceiling_GBps: the best of one 2 GiB cudaMemcpyAsync, 2 and 4 such copies "
+                   "at once on separate streams, and the SMs storing constants straight into the "
+                   "pinned buffer (sq_fill_u32), all into the same pinned memory",
            "path": "direct: kernels store into pinned host memory" if dt_direct <= dt_copy else
                    "copy: 2 GiB device chunks, cudaMemcpyAsync to pinned host, 2 streams",
            "copy_ms_per_step": dt_copy * 1000, "direct_ms_per_step": dt_direct * 1000}
+    del link_stage
     del host64, host32, stage
     return res
 
@@ -571,7 +631,10 @@ def _time_launches(torch, fn, reps, stream):
     return a.elapsed_time(b) / reps
 
 
-def breakdown(torch, sq, C, workloads, dev, ms32_plain, tuned_from_file=False):
+def breakdown(torch, sq, C, workloads, dev, ms32_plain, tuned_from_file=False, with_oracle=True):
+    """Every other configuration of the benchmark suite, measured outside the
+    timed region; with_oracle adds the oracle's rate on the host cores to each
+    configuration's row and the transforms' error against FP64."""
     import numpy as np
 
     out = {}
@@ -579,6 +642,21 @@ def breakdown(torch, sq, C, workloads, dev, ms32_plain, tuned_from_file=False):
     sh = lambda: int(stream.cuda_stream)  # noqa: E731
     plain_rate = N32 / (ms32_plain / 1e3)
     out["squares32_plain"] = {"Gsamples_per_s": plain_rate / 1e9, "GBps": plain_rate * 4 / 1e9}
+
+    # squares32 from counter 0, first key of seed 1, 2^24 outputs (the parity
+    # configuration; its 64 MiB of output fits in L2)
+    key1 = int(sq.make_keys(1, 1)[0])
+    n1 = 1 << 24
+    buf1 = torch.empty(n1, dtype=torch.int32, device=dev)
+    ms = _time_launches(torch, lambda: C.sq_u32(key1, 0, n1, buf1.data_ptr(), sh()), 20, stream)
+    out["single_2p24"] = {"Gsamples_per_s": n1 / (ms / 1e3) / 1e9, "ms": ms,
+                          "note": "64 MiB of output: L2-resident writes"}
+    if with_oracle:
+        out["single_2p24"]["cpu_baseline"] = oracle_rate_pair(
+            lambda th: __import__("oracle").fill32(key1, 0, n1, threads=th), n1,
+            lambda th: __import__("oracle").fill32(key1, 0, n1 >> 2, threads=th), n1 >> 2,
+            "all 2^24 outputs of the configuration", "the first 2^22 outputs")
+    del buf1
 
     # ragged batch, 4096 streams, one persistent launch replayed from a CUDA graph
     b = workloads.ragged_batch(4096, seed=7)
@@ -591,7 +669,7 @@ def breakdown(torch, sq, C, workloads, dev, ms32_plain, tuned_from_file=False):
     if not tuned_from_file:
         C.sq_autotune_batch(keys.data_ptr(), bases.data_ptr(), lengths.data_ptr(),
                             offsets.data_ptr(), b.nstreams, outb.data_ptr())
-    cfgb = C.sq_get_config(C.SQ_KERNEL_BATCH, 0)
+    cfgb = C.sq_get_config(C.SQ_KERNEL_BATCH, b.nstreams)
 
     def run_batch():
         C.sq_batch(keys.data_ptr(), bases.data_ptr(), lengths.data_ptr(), offsets.data_ptr(),
@@ -604,6 +682,8 @@ def breakdown(torch, sq, C, workloads, dev, ms32_plain, tuned_from_file=False):
         "GBps": rate_b * 4 / 1e9, "per_sample_vs_plain": rate_b / plain_rate,
         "launch": [C.sq_variant_name(2, cfgb.variant), cfgb.block, cfgb.ctas_per_sm],
         "timing": "CUDA graph of one persistent launch, 10 replays"}
+    if with_oracle:
+        out["batched_ragged"]["cpu_baseline"] = oracle_batch_rate(np, b)
     del outb, keys, bases, lengths, offsets
     torch.cuda.empty_cache()
 
@@ -631,6 +711,10 @@ def breakdown(torch, sq, C, workloads, dev, ms32_plain, tuned_from_file=False):
         ms = _time_launches(torch, lambda: fn(key, 0, n, buf.data_ptr(), sh()), 10, stream)
         out[name] = {"Gsamples_per_s": n / (ms / 1e3) / 1e9, "GBps": n * es / (ms / 1e3) / 1e9,
                      "ms": ms}
+        if with_oracle and name in ("uniform_f32", "uniform_bf16", "normal_f32"):
+            torch.cuda.synchronize()
+            out[name]["precision"] = transform_precision(torch, np, name, buf, key, n)
+            out[name]["cpu_baseline"] = oracle_transform_rate(name, key)
 
     # strided counters (Section 4's increments other than one), 2^30 outputs
     for name, fn, es in (("u32_stride3", C.sq_u32_strided, 4), ("u64_stride3", C.sq_u64_strided, 8)):
@@ -671,16 +755,120 @@ def breakdown(torch, sq, C, workloads, dev, ms32_plain, tuned_from_file=False):
     rate = S * cps / (ms / 1e3)
     out["fused_stats"] = {"Gsamples_per_s": rate / 1e9, "ms": ms,
                           "frac_int": rate / (lane_cycles / HEAVY_CYCLES_SQ32)}
+    if with_oracle:
+        fkeys = sq.make_keys(13, 1 << 14)
+        fbases = np.zeros(1 << 14, dtype=np.uint64)
+        out["fused_stats"]["cpu_baseline"] = oracle_rate_pair(
+            lambda th: __import__("oracle").fused_stats(fkeys, fbases, cps, threads=th), (1 << 14) * cps,
+            lambda th: __import__("oracle").fused_stats(fkeys[:1 << 8], fbases[:1 << 8], cps, threads=th),
+            (1 << 8) * cps, "the first 2^14 of the 2^20 streams, all 2^18 counters each",
+            "the first 2^8 streams")
 
     # context: cuRAND Philox4x32-10 (library call) on the same GPU
     out["curand_philox4x32_10"] = curand_context(torch, dev, stream)
     return out
 
 
+def oracle_rate_pair(run_all, n_all, run_one, n_one, sample_all, sample_one):
+    """The oracle as it stands, timed on all host cores and on one: run_all /
+    run_one take a thread count and compute n_all / n_one samples."""
+    import oracle
+
+    threads = oracle.default_threads()
+    run_one(1)  # load the library outside the timing
+    t0 = time.perf_counter()
+    run_all(threads)
+    dt = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    run_one(1)
+    dt1 = time.perf_counter() - t1
+    return {"value": n_all / dt / 1e9, "unit": "Gsamples/s", "cores": threads, "kind": "oracle",
+            "sample": f"{sample_all}; {dt:.2f} s wall",
+            "single_thread": {"value": n_one / dt1 / 1e9, "unit": "Gsamples/s",
+                              "sample": f"{sample_one}; {dt1:.2f} s wall"}}
+
+
+def oracle_batch_rate(np, b, prefix=1 << 29):
+    """oracle.batch32 on the first streams of the batch holding at most
+    `prefix` samples, the streams split over the host cores (each thread
+    writes its streams' disjoint ranges of one array)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+
+    keys = oracle.make_keys(b.key_seed, b.nstreams)
+    ends = b.offsets + b.lengths
+    k = max(1, int(np.searchsorted(ends, prefix, side="right")))
+    total = int(ends[k - 1])
+    res = np.empty(total, dtype=np.uint32)
+
+    def run(threads, kk):
+        parts = np.array_split(np.arange(kk), threads)
+        with ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(lambda idx: oracle.batch32(keys[idx], b.bases[idx], b.lengths[idx],
+                                                   b.offsets[idx], res) if idx.size else None,
+                        parts))
+
+    k1 = max(1, int(np.searchsorted(ends, prefix >> 4, side="right")))
+    return oracle_rate_pair(lambda th: run(th, k), total, lambda th: run(1, k1), int(ends[k1 - 1]),
+                            f"the first {k} of {b.nstreams} streams ({total} samples)",
+                            f"the first {k1} streams ({int(ends[k1 - 1])} samples)")
+
+
+def oracle_transform_rate(name, key):
+    """The oracle's transform (FP32/BF16 uniforms, FP64 normals) on 2^27
+    outputs on all host cores and 2^23 on one."""
+    import oracle
+
+    fn = {"uniform_f32": oracle.uniform_f32, "uniform_bf16": oracle.uniform_bf16,
+          "normal_f32": oracle.normal_f64}[name]
+    return oracle_rate_pair(lambda th: fn(key, 0, 1 << 27, threads=th), 1 << 27,
+                            lambda th: fn(key, 0, 1 << 23, threads=th), 1 << 23,
+                            "the first 2^27 outputs of the configuration", "the first 2^23 outputs")
+
+
+def transform_precision(torch, np, name, buf, key, n, chunk=1 << 26):
+    """Error of the GPU transform over all n outputs in `buf` (counter base
+    0) against the oracle, chunk by chunk: uniforms as mismatching bit
+    patterns (0 is exact), normals as max absolute error where |z| < 5, max
+    relative error where |z| >= 5, the number of such tail values and the
+    largest |z|."""
+    import oracle
+
+    if name == "normal_f32":
+        max_abs = max_rel = max_z = 0.0
+        tail = 0
+        for a in range(0, n, chunk):
+            m = min(chunk, n - a)
+            z = buf[4 * a:4 * (a + m)].view(torch.float32).cpu().numpy().astype(np.float64)
+            ref = oracle.normal_f64(key, a // 2, m)
+            err = np.abs(z - ref)
+            core = np.abs(ref) < 5
+            if core.any():
+                max_abs = max(max_abs, float(err[core].max()))
+            if (~core).any():
+                max_rel = max(max_rel, float((err[~core] / np.abs(ref[~core])).max()))
+                tail += int((~core).sum())
+            max_z = max(max_z, float(np.abs(ref).max()))
+        return {"outputs": n, "reference": "oracle Box-Muller in FP64 on the same integers",
+                "max_abs_core": max_abs, "max_rel_tail": max_rel, "tail_count": tail,
+                "max_abs_z": max_z, "bound_abs_core": 2e-6, "bound_rel_tail": 1e-5}
+    es, ref_fn, dt = ((4, oracle.uniform_f32, np.uint32) if name == "uniform_f32"
+                      else (2, oracle.uniform_bf16, np.uint16))
+    bad = 0
+    for a in range(0, n, chunk):
+        m = min(chunk, n - a)
+        got = buf[es * a:es * (a + m)].cpu().numpy().view(dt)
+        bad += int(np.count_nonzero(got != ref_fn(key, a, m).view(dt)))
+    return {"outputs": n, "mismatching_bit_patterns": bad,
+            "reference": "oracle: floor(squares32 / 2^8) 2^-24" +
+                         (", rounded toward zero to bfloat16" if name == "uniform_bf16" else "")}
+
+
 def _batch_regime(torch, sq, C, workloads, np, dev, stream, sh, S, lo, hi, plain_rate):
     """One ragged batch of S streams of log-uniform length in [lo, hi), timed
-    in the configuration sq_autotune_batch picks for it; the batch kernel's
-    previous configuration is restored afterwards."""
+    in the configuration sq_autotune_batch picks for it (kept in the batch
+    table's entry for S streams)."""
     bs = workloads.ragged_batch(S, seed=7, lo=lo, hi=hi)
     keys = torch.from_numpy(sq.make_keys(bs.key_seed, bs.nstreams).view(np.int64)).to(dev)
     bases = torch.from_numpy(bs.bases.view(np.int64)).to(dev)
@@ -688,17 +876,15 @@ def _batch_regime(torch, sq, C, workloads, np, dev, stream, sh, S, lo, hi, plain
     offsets = torch.from_numpy(bs.offsets).to(dev)
     outb = torch.empty(bs.total, dtype=torch.int32, device=dev)
     torch.cuda.synchronize()
-    saved = C.sq_get_config(C.SQ_KERNEL_BATCH, 0)
     C.sq_autotune_batch(keys.data_ptr(), bases.data_ptr(), lengths.data_ptr(),
                         offsets.data_ptr(), bs.nstreams, outb.data_ptr())
-    cfg = C.sq_get_config(C.SQ_KERNEL_BATCH, 0)
+    cfg = C.sq_get_config(C.SQ_KERNEL_BATCH, bs.nstreams)
 
     def run():
         C.sq_batch(keys.data_ptr(), bases.data_ptr(), lengths.data_ptr(), offsets.data_ptr(),
                    bs.nstreams, outb.data_ptr(), sh())
 
     ms = _time_graph(torch, run, 10, stream)
-    C.sq_set_config(C.SQ_KERNEL_BATCH, 0, saved.variant, saved.block, saved.ctas_per_sm)
     rate = bs.total / (ms / 1e3)
     return {"streams": bs.nstreams, "mean_length": bs.total / bs.nstreams, "samples": bs.total,
             "ms": ms, "Gsamples_per_s": rate / 1e9, "per_sample_vs_plain": rate / plain_rate,
