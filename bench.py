@@ -71,6 +71,8 @@ def parse_args():
                                          "batch_short", "batch_tiny", "batch_mid"],
                    help="run one kernel on a small case (for ncu) instead of the benchmark")
     p.add_argument("--profile-n", type=int, default=1 << 28)
+    p.add_argument("--profile-variant", help="batch variant name for the batch_* profile cases "
+                                             "(default: the one named in the case)")
     p.add_argument("--reference-budget-s", type=float, default=60.0,
                    help="wall time the reference arm aims to spend on its K steps")
     return p.parse_args()
@@ -393,7 +395,11 @@ def run_ours(args, rank, world, local):
         r_int32 = lane_cycles / HEAVY_CYCLES_SQ32
         r_int64 = lane_cycles / HEAVY_CYCLES_SQ64
         store = store_ceiling(torch, C, out32, N32, stream)
-        store_gbs = store["GBps"]
+        # The ceiling of DRAM writes: the best of the write-only sweep and of
+        # what the squares64 launches of the timed region themselves wrote.
+        store_gbs = max(store["GBps"], r64 * 8 / 1e9)
+        store_src = ("sq_fill_u32 sweep" if store["GBps"] >= r64 * 8 / 1e9
+                     else "squares64 launches of the timed region (above the sq_fill_u32 sweep)")
         # Bound from the counters: the squares32 kernel runs as fast without
         # its stores as with them and its FMA-heavy pipe is the busiest unit
         # (profiles/sq_u32_plain_2p28.md), so it is bound by integer issue,
@@ -410,15 +416,17 @@ def run_ours(args, rank, world, local):
             "peak_source": f"integer model: {sms} SMs x {LANES_PER_SM} lanes x {sm_max} MHz / "
                            f"{HEAVY_CYCLES_SQ32} FMA-heavy cycles per warp-sample = "
                            f"{r_int32 / 1e9:.0f} Gsamples/s; hbm copy {hbm} GB/s ({peak_src}, "
-                           f"MEASURED_PEAKS.json); store-only ceiling measured here with "
-                           f"sq_fill_u32 (best of {store['configs']} launch configurations)",
+                           f"MEASURED_PEAKS.json); store-only ceiling: the best DRAM write rate measured here, "
+                           f"of {store['configs']} sq_fill_u32 shapes and the squares64 launches",
             "limiter": "FMA-heavy pipe (ncu: busiest unit; the kernel without stores takes the "
                        "same time as with them)",
             "achieved_GBps": r32 * 4 / 1e9,
             "frac_hbm": (r32 * 4 / 1e9) / hbm,
             "peak_store_only": store_gbs,
             "frac_store_only": (r32 * 4 / 1e9) / store_gbs,
-            "store_only_config": store["best"],
+            "store_only_source": store_src,
+            "store_only_sweep": {"GBps": store["GBps"], "best": store["best"],
+                                 "configs": store["configs"]},
             "frac_int": r32 / r_int32,
             "squares64": {"avg_launch_ms": ms64, "Gsamples_per_s": r64 / 1e9,
                           "GBps": r64 * 8 / 1e9, "bound": "hbm" if store_gbs * 1e9 / 8 < r_int64 else "alu",
@@ -469,27 +477,30 @@ def store_ceiling(torch, C, buf, n, stream, reps=3):
     """Write-only ceiling of HBM for the generators' store path: sq_fill_u32
     (their chunking, grid and store variants, no arithmetic) over n uint32
     elements of `buf`, in every store variant, block size and CTA count the
-    plain kernels use; CUDA events on `stream`. Returns the best rate (GB/s
-    written), its configuration and how many were timed."""
+    plain kernels use, and paced (each thread pausing after each chunk) in
+    the few-thread shapes where a flood of stores is slower than a paced
+    stream; CUDA events on `stream`. Returns the best rate (GB/s written),
+    its configuration and pause, and how many were timed."""
     sh = int(stream.cuda_stream)
-    best, best_cfg, count = 0.0, None, 0
-    for v in range(C.sq_num_variants(C.SQ_KERNEL_U32)):
-        for block in (128, 256, 512):
-            for ctas in (1, 2, 4, 0):
-                cfg = (v, block, ctas)
-                C.sq_fill_u32(0x5A5A5A5A, n, buf.data_ptr(), cfg, sh)
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                for _ in range(reps):
-                    C.sq_fill_u32(0x5A5A5A5A, n, buf.data_ptr(), cfg, sh)
-                b.record(stream)
-                torch.cuda.synchronize()
-                gbs = n * 4 * reps / (a.elapsed_time(b) / 1e3) / 1e9
-                count += 1
-                if gbs > best:
-                    best, best_cfg = gbs, [C.sq_variant_name(C.SQ_KERNEL_U32, v), block, ctas]
-    return {"GBps": best, "best": best_cfg, "configs": count}
+    shapes = [((v, block, ctas), 0) for v in range(C.sq_num_variants(C.SQ_KERNEL_U32))
+              for block in (128, 256, 512) for ctas in (1, 2, 4, 0)]
+    shapes += [((v, block, ctas), pause) for v in (0, 1, 4, 5) for block in (128, 256)
+               for ctas in (1, 2) for pause in (64, 128, 256, 512)]
+    best, best_cfg = 0.0, None
+    for cfg, pause in shapes:
+        C.sq_fill_u32(0x5A5A5A5A, n, buf.data_ptr(), cfg, pause, sh)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            C.sq_fill_u32(0x5A5A5A5A, n, buf.data_ptr(), cfg, pause, sh)
+        b.record(stream)
+        torch.cuda.synchronize()
+        gbs = n * 4 * reps / (a.elapsed_time(b) / 1e3) / 1e9
+        if gbs > best:
+            best = gbs
+            best_cfg = [C.sq_variant_name(C.SQ_KERNEL_U32, cfg[0]), cfg[1], cfg[2], f"pause {pause} ns"]
+    return {"GBps": best, "best": best_cfg, "configs": len(shapes)}
 
 
 def e2e_block(torch, C, key, base64, base32, dev, steps):
@@ -564,7 +575,7 @@ def e2e_block(torch, C, key, base64, base32, dev, steps):
         return run
 
     def run_fill():
-        C.sq_fill_u32(0x5A5A5A5A, N32, host32.data_ptr(), None, int(streams[0].cuda_stream))
+        C.sq_fill_u32(0x5A5A5A5A, N32, host32.data_ptr(), None, 0, int(streams[0].cuda_stream))
         streams[0].synchronize()
 
     dt_copy = timed(run_copy)
@@ -746,6 +757,12 @@ def breakdown(torch, sq, C, workloads, dev, ms32_plain, tuned_from_file=False, w
     fs = torch.empty(S, dtype=torch.int64, device=dev)
     fh = torch.empty(256, dtype=torch.int64, device=dev)
     torch.cuda.synchronize()
+    if not tuned_from_file:
+        # tuned on 2^14 of the streams (2^32 counters), applied to the full size
+        C.sq_autotune(C.SQ_KERNEL_FUSED, (1 << 14) * cps)
+        cf = C.sq_get_config(C.SQ_KERNEL_FUSED, (1 << 14) * cps)
+        C.sq_set_config(C.SQ_KERNEL_FUSED, S * cps, cf.variant, cf.block, cf.ctas_per_sm)
+    cfgf = C.sq_get_config(C.SQ_KERNEL_FUSED, S * cps)
     ms = _time_launches(torch, lambda: C.sq_fused_stats(fk.data_ptr(), fb.data_ptr(), S, cps,
                                                         fx.data_ptr(), fs.data_ptr(),
                                                         fh.data_ptr(), sh()), 3, stream)
@@ -754,7 +771,9 @@ def breakdown(torch, sq, C, workloads, dev, ms32_plain, tuned_from_file=False, w
     lane_cycles = props.multi_processor_count * LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6
     rate = S * cps / (ms / 1e3)
     out["fused_stats"] = {"Gsamples_per_s": rate / 1e9, "ms": ms,
-                          "frac_int": rate / (lane_cycles / HEAVY_CYCLES_SQ32)}
+                          "frac_int": rate / (lane_cycles / HEAVY_CYCLES_SQ32),
+                          "launch": [C.sq_variant_name(C.SQ_KERNEL_FUSED, cfgf.variant), cfgf.block,
+                                     cfgf.ctas_per_sm]}
     if with_oracle:
         fkeys = sq.make_keys(13, 1 << 14)
         fbases = np.zeros(1 << 14, dtype=np.uint64)
@@ -769,6 +788,18 @@ def breakdown(torch, sq, C, workloads, dev, ms32_plain, tuned_from_file=False, w
     return out
 
 
+def _repeat_timed(fn, threads, min_s=0.3, max_reps=64):
+    """Seconds per call of fn(threads), repeating short calls until at least
+    min_s have passed; returns (seconds per call, calls)."""
+    reps, total = 0, 0.0
+    while reps < max_reps and (reps == 0 or total < min_s):
+        t0 = time.perf_counter()
+        fn(threads)
+        total += time.perf_counter() - t0
+        reps += 1
+    return total / reps, reps
+
+
 def oracle_rate_pair(run_all, n_all, run_one, n_one, sample_all, sample_one):
     """The oracle as it stands, timed on all host cores and on one: run_all /
     run_one take a thread count and compute n_all / n_one samples."""
@@ -776,16 +807,12 @@ def oracle_rate_pair(run_all, n_all, run_one, n_one, sample_all, sample_one):
 
     threads = oracle.default_threads()
     run_one(1)  # load the library outside the timing
-    t0 = time.perf_counter()
-    run_all(threads)
-    dt = time.perf_counter() - t0
-    t1 = time.perf_counter()
-    run_one(1)
-    dt1 = time.perf_counter() - t1
+    dt, r = _repeat_timed(run_all, threads)
+    dt1, r1 = _repeat_timed(run_one, 1)
     return {"value": n_all / dt / 1e9, "unit": "Gsamples/s", "cores": threads, "kind": "oracle",
-            "sample": f"{sample_all}; {dt:.2f} s wall",
+            "sample": f"{sample_all}; {dt:.3f} s per call, {r} calls",
             "single_thread": {"value": n_one / dt1 / 1e9, "unit": "Gsamples/s",
-                              "sample": f"{sample_one}; {dt1:.2f} s wall"}}
+                              "sample": f"{sample_one}; {dt1:.3f} s per call, {r1} calls"}}
 
 
 def oracle_batch_rate(np, b, prefix=1 << 29):
@@ -957,6 +984,7 @@ def profile_case(args):
                "batch_tiny": (1 << 22, 3, 30, "flat-warp", 512)}
     if args.profile in regimes:
         S, lo, hi, vname, block = regimes[args.profile]
+        vname = args.profile_variant or vname
         bt = workloads.ragged_batch(S, seed=7, lo=lo, hi=hi)
         k = torch.from_numpy(sq.make_keys(7, bt.nstreams).view(np.int64)).to(dev)
         bb = torch.from_numpy(bt.bases.view(np.int64)).to(dev)
@@ -989,7 +1017,7 @@ def profile_case(args):
     print(f"profile config: {C.sq_variant_name(kids[args.profile], c.variant)} block {c.block} "
           f"ctas/SM {c.ctas_per_sm}", flush=True)
     if args.profile == "fused":
-        S, cps = max(1, n >> 18), 1 << 18
+        S, cps = max(1, n >> 18), 1 << 18  # --profile-n 2^30: 2^12 streams, ~1,600 counters per lane per item
         k = torch.from_numpy(sq.make_keys(13, S).view(np.int64)).to(dev)
         b = torch.zeros(S, dtype=torch.int64, device=dev)
         x = torch.empty(S, dtype=torch.int32, device=dev)

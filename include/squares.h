@@ -234,7 +234,9 @@ typedef struct {
     int32_t variant;     /* kernel body: store width / cache policy, see sq_variant_name;
                           * for SQ_KERNEL_BATCH 0-3 tile the packed output, 4-8 give each
                           * stream to 32, 8, 16, 4 or 1 lanes, 9 lays 32 streams end to
-                          * end per warp (4-9 are for many short streams) */
+                          * end per warp, 10 and 11 do the same with runs of 4 or 8
+                          * consecutive values per lane (4-11 are for many short
+                          * streams) */
     int32_t block;       /* threads per CTA: 128, 256 or 512 (SQ_KERNEL_BATCH also 64) */
     int32_t ctas_per_sm; /* persistent grid = SMs * ctas_per_sm; 0 = max resident */
     int32_t reserved;
@@ -291,11 +293,14 @@ int sq_autotune_load(const char *path);
  * write bandwidth those kernels are held against, for device memory or,
  * given host memory the device can write, for the host link. cfg selects
  * the variant, block and CTAs per SM as for SQ_KERNEL_U32 (NULL: the entry
- * sq_u32 would use for n). out [device or device-writable host], 4-byte
- * aligned. Errors as for sq_u32, and SQ_EINVAL for an invalid cfg. No
- * counterpart in the paper: a measurement kernel. */
+ * sq_u32 would use for n). pause_ns > 0 makes every thread pause that long
+ * (__nanosleep) after each chunk it stores: a paced store stream, like a
+ * generator's, can reach more DRAM write bandwidth than one that floods
+ * the memory system. out [device or device-writable host], 4-byte aligned.
+ * Errors as for sq_u32, and SQ_EINVAL for an invalid cfg. No counterpart
+ * in the paper: a measurement kernel. */
 int sq_fill_u32(uint32_t value, size_t n, uint32_t *out, const sq_launch_config *cfg,
-                sq_stream_t stream);
+                uint32_t pause_ns, sq_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * CUDA graph of one sq_batch launch, for callers without a graph API of

@@ -64,7 +64,7 @@ _SIGNATURES = {
     "sq_keys_u64": [_p, _sz, _u64, _p, _p],
     "sq_uniform2_f32": [_u64, _u64, _sz, _p, _p],
     "sq_uniform_f64": [_u64, _u64, _sz, _p, _p],
-    "sq_fill_u32": [ctypes.c_uint32, _sz, _p, ctypes.POINTER(sq_launch_config), _p],
+    "sq_fill_u32": [ctypes.c_uint32, _sz, _p, ctypes.POINTER(sq_launch_config), ctypes.c_uint32, _p],
     "sq_batch": [_p, _p, _p, _p, _sz, _p, _p],
     "sq_batch_validate": [_p, _p, _sz, _p],
     "sq_uniform_f32": [_u64, _u64, _sz, _p, _p],
@@ -185,10 +185,10 @@ def sq_uniform_f64(key: int, ctr_base: int, n: int, out_ptr: int, stream: int = 
 
 
 def sq_fill_u32(value: int, n: int, out_ptr: int, config: tuple | None = None,
-                stream: int = 0) -> None:
+                pause_ns: int = 0, stream: int = 0) -> None:
     """config: (variant, block, ctas_per_sm) as for SQ_KERNEL_U32, or None."""
     cfg = None if config is None else ctypes.byref(sq_launch_config(*config, 0))
-    _call("sq_fill_u32", value, n, out_ptr, cfg, stream)
+    _call("sq_fill_u32", value, n, out_ptr, cfg, pause_ns, stream)
 
 
 def sq_batch(keys_ptr: int, bases_ptr: int, lengths_ptr: int, offsets_ptr: int, nstreams: int,

@@ -340,7 +340,7 @@ int sq_uniform_f64(uint64_t key, uint64_t ctr_base, size_t n, double *out, sq_st
 }
 
 int sq_fill_u32(uint32_t value, size_t n, uint32_t *out, const sq_launch_config *cfg,
-                sq_stream_t stream) {
+                uint32_t pause_ns, sq_stream_t stream) {
     if (n == 0) return ok();
     if (out == nullptr) return fail(SQ_EINVAL, "sq_fill_u32: out is NULL with n = %zu", n);
     if (!aligned(out, 4)) return fail(SQ_EINVAL, "sq_fill_u32: out is not 4-byte aligned");
@@ -353,7 +353,8 @@ int sq_fill_u32(uint32_t value, size_t n, uint32_t *out, const sq_launch_config 
                         c.variant, c.block, c.ctas_per_sm);
     }
     if (injected("sq_fill_u32")) return injected_fail("sq_fill_u32");
-    const cudaError_t e = sq::launch_plain(sq::kFillKernelId, c, value, 0, n, out, static_cast<cudaStream_t>(stream));
+    const cudaError_t e = sq::launch_plain(sq::kFillKernelId, c, value, pause_ns, n, out,
+                                           static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "sq_fill_u32");
     return ok();
 }

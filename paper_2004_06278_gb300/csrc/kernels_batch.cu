@@ -357,6 +357,66 @@ __device__ __forceinline__ void flat_walk(const FlatEntry *table, Pos Pe, Pos T,
 // more. A clamped length is also capped at 2^57 so that the 64-bit scan
 // cannot overflow; every write then lies inside its owner's clamped range,
 // whatever the metadata.
+// One group of 32 streams of a flattened warp: lane L's stream g + L, its
+// length clamped to the batch extent (0 for a negative offset, at most
+// 2^57), and its first position P in the warp's value sequence (exclusive
+// scan of the lengths; T values in all).
+struct FlatGroup {
+    int64_t len, off, P, T;
+    uint64_t key, base;
+    uint32_t nonempty;  // lanes with len > 0
+};
+
+__device__ __forceinline__ FlatGroup flat_group(const uint64_t *__restrict__ keys,
+                                                const uint64_t *__restrict__ bases,
+                                                const int64_t *__restrict__ lengths,
+                                                const int64_t *__restrict__ offsets, uint32_t S,
+                                                int64_t end, uint64_t g, uint32_t lane) {
+    constexpr int64_t kLenCap = int64_t{1} << 57;
+    FlatGroup fg{0, 0, 0, 0, 0, 0, 0};
+    const uint64_t s = g + lane;
+    if (s < S) {
+        fg.len = __ldg(lengths + s);
+        fg.off = __ldg(offsets + s);
+        fg.key = __ldg(keys + s);
+        fg.base = __ldg(bases + s);
+    }
+    if (fg.off < 0) fg.len = 0;
+    else if (fg.len > end - fg.off) fg.len = end - fg.off;
+    if (fg.len < 0) fg.len = 0;
+    if (fg.len > kLenCap) fg.len = kLenCap;
+    int64_t inc = fg.len;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int64_t o = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+        if (lane >= static_cast<uint32_t>(d)) inc += o;
+    }
+    fg.P = inc - fg.len;
+    fg.T = __shfl_sync(0xFFFFFFFFu, inc, 31);
+    fg.nonempty = __ballot_sync(0xFFFFFFFFu, fg.len > 0);
+    return fg;
+}
+
+// The group's walk one position per lane per step (see flat_walk): the
+// non-empty streams' entries go, in order, to the warp's table.
+__device__ __forceinline__ void flat_positions(FlatEntry *table, const FlatGroup &fg,
+                                               uint32_t *__restrict__ out, uint32_t lane) {
+    if (fg.len > 0) {
+        FlatEntry &e = table[__popc(fg.nonempty & ((1u << lane) - 1u))];
+        e.y0 = (fg.base - static_cast<uint64_t>(fg.P)) * fg.key;
+        e.dst = reinterpret_cast<uint64_t>(out) + static_cast<uint64_t>(fg.off - fg.P) * 4u;
+        e.key = fg.key;
+    }
+    __syncwarp();
+    if (fg.T < (int64_t{1} << 31))
+        flat_walk<uint32_t>(table, fg.len > 0 ? static_cast<uint32_t>(fg.P) : 0xC0000000u,
+                            static_cast<uint32_t>(fg.T), lane);
+    else
+        flat_walk<uint64_t>(table, fg.len > 0 ? static_cast<uint64_t>(fg.P) : 0xC000000000000000ull,
+                            static_cast<uint64_t>(fg.T), lane);
+    __syncwarp();
+}
+
 __global__ void __launch_bounds__(512)
     batch_flat_kernel(const uint64_t *__restrict__ keys, const uint64_t *__restrict__ bases,
                       const int64_t *__restrict__ lengths, const int64_t *__restrict__ offsets,
@@ -367,54 +427,138 @@ __global__ void __launch_bounds__(512)
     const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const uint64_t stride = ((static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5) * 32;
     const int64_t end = __ldg(offsets + S - 1) + __ldg(lengths + S - 1);
-    constexpr int64_t kLenCap = int64_t{1} << 57;
-    for (uint64_t g = warp * 32; g < S; g += stride) {
-        const uint64_t s = g + lane;
-        int64_t len = 0, off = 0;
-        uint64_t key = 0, base = 0;
-        if (s < S) {
-            len = __ldg(lengths + s);
-            off = __ldg(offsets + s);
-            key = __ldg(keys + s);
-            base = __ldg(bases + s);
-        }
-        if (off < 0) len = 0;
-        else if (len > end - off) len = end - off;
-        if (len < 0) len = 0;
-        if (len > kLenCap) len = kLenCap;
-        int64_t inc = len;
+    for (uint64_t g = warp * 32; g < S; g += stride)
+        flat_positions(table, flat_group(keys, bases, lengths, offsets, S, end, g, lane), out, lane);
+}
+
+// Flattened warps with runs (variants 10 and 11, C = 4 or 8), for the same
+// batches: the group's 32 streams are laid end to end as in batch_flat_kernel,
+// but each lane takes a run of C consecutive positions per step (the warp
+// 32 * C), so the owner is looked up once per run and consecutive values of
+// a stream follow by Weyl addition (y += key), as in the plain kernels.
+// Where the group's streams are packed (each non-empty stream's output
+// starts where the previous one's ends, as an exclusive prefix sum of the
+// lengths gives), position p's output is dst[p] for one dst, and the runs
+// are placed so that each run is one aligned C * 4-byte vector store; a run
+// that reaches before position 0 or past the group's end is stored element
+// by element. A group with gaps or overlaps between its streams, or with
+// 2^30 values or more, takes batch_flat_kernel's walk instead, so every
+// write stays inside its owner's clamped range whatever the metadata.
+//
+// Run walk: the warp's stream starts P (one per lane, non-decreasing, P of
+// lane 0 is 0) give the owner of a position q as the last lane L with
+// P_L <= q (empty streams share the next stream's start and are passed
+// over), found by a binary search over the lanes with shuffles. The table
+// holds, per lane, the stream's Weyl term at its first position (ctr_base *
+// key), its key, its first and end positions and the lane that owns its
+// end position; a run that reaches the end of its stream continues with
+// that entry.
+struct alignas(16) RunEntry {
+    uint64_t ys;
+    uint64_t key;
+    uint32_t P;
+    uint32_t E;
+    uint32_t nxt;
+    uint32_t pad;
+};
+static_assert(sizeof(RunEntry) == sizeof(FlatEntry), "run and flat tables share the warp's slots");
+
+// Last lane L with P_L <= q, given the lanes' non-decreasing P and P_0 <= q.
+__device__ __forceinline__ uint32_t owner_lane(uint32_t P, uint32_t q) {
+    uint32_t k = 0;
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int64_t o = __shfl_up_sync(0xFFFFFFFFu, inc, d);
-            if (lane >= static_cast<uint32_t>(d)) inc += o;
+    for (uint32_t step = 16; step > 0; step >>= 1) {
+        const uint32_t pc = __shfl_sync(0xFFFFFFFFu, P, k + step);
+        if (pc <= q) k += step;
+    }
+    return k;
+}
+
+template <int C>
+__device__ __forceinline__ void run_walk(RunEntry *tab, const FlatGroup &fg, uint32_t *__restrict__ dst,
+                                         uint32_t lane) {
+    const int32_t T = static_cast<int32_t>(fg.T);
+    const uint32_t P = static_cast<uint32_t>(fg.P);
+    const uint32_t E = P + static_cast<uint32_t>(fg.len);
+    tab[lane] = RunEntry{fg.base * fg.key, fg.key, P, E, owner_lane(P, E), 0u};
+    __syncwarp();
+    // dst[0] lies `a` elements past a C * 4-byte boundary: runs start at
+    // positions -a + C * j, so that every run's vector store is aligned.
+    const int32_t a = static_cast<int32_t>((reinterpret_cast<uintptr_t>(dst) >> 2) % C);
+    for (int32_t b = -a; b < T; b += 32 * C) {
+        const int32_t q = b + static_cast<int32_t>(lane) * C;
+        const uint32_t qc = q < 0 ? 0u : static_cast<uint32_t>(q < T ? q : T - 1);
+        const uint32_t k = owner_lane(P, qc);
+        if (q < T) {
+            const RunEntry e = tab[k];
+            uint64_t y = e.ys + static_cast<uint64_t>(static_cast<int64_t>(q) - static_cast<int64_t>(e.P)) * e.key;
+            uint64_t key = e.key;
+            int32_t stop = static_cast<int32_t>(e.E);
+            uint32_t nx = e.nxt;
+            uint32_t w[C];
+#pragma unroll
+            for (int i = 0; i < C; ++i) {
+                // At the end of the stream, the next non-empty one starts with
+                // its first value. (At the group's end, T, the entry taken is
+                // some lane's and the values past T are not stored.)
+                if (q + i == stop) {
+                    const RunEntry f = tab[nx];
+                    y = f.ys;
+                    key = f.key;
+                    stop = static_cast<int32_t>(f.E);
+                    nx = f.nxt;
+                }
+                const uint64_t z = add64(y, key);
+                w[i] = squares32_yz(y, z);
+                y = z;
+            }
+            if (q >= 0 && q + C <= T) {
+                if constexpr (C == 8)
+                    store32B<false>(dst + q, w);
+                else
+                    store16B<false>(dst + q, w[0], w[1], w[2], w[3]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < C; ++i)
+                    if (q + i >= 0 && q + i < T) dst[q + i] = w[i];
+            }
         }
-        const int64_t P = inc - len;
-        const int64_t T = __shfl_sync(0xFFFFFFFFu, inc, 31);
-        const uint32_t nonempty = __ballot_sync(0xFFFFFFFFu, len > 0);
-        if (len > 0) {
-            FlatEntry &e = table[__popc(nonempty & ((1u << lane) - 1u))];
-            e.y0 = (base - static_cast<uint64_t>(P)) * key;
-            e.dst = reinterpret_cast<uint64_t>(out) + static_cast<uint64_t>(off - P) * 4u;
-            e.key = key;
-        }
-        __syncwarp();
-        if (T < (int64_t{1} << 31))
-            flat_walk<uint32_t>(table, len > 0 ? static_cast<uint32_t>(P) : 0xC0000000u,
-                                static_cast<uint32_t>(T), lane);
+    }
+    __syncwarp();
+}
+
+template <int C>
+__global__ void __launch_bounds__(512)
+    batch_run_kernel(const uint64_t *__restrict__ keys, const uint64_t *__restrict__ bases,
+                     const int64_t *__restrict__ lengths, const int64_t *__restrict__ offsets,
+                     uint32_t S, uint32_t *__restrict__ out) {
+    extern __shared__ FlatEntry flat_tables[];
+    FlatEntry *table = flat_tables + (threadIdx.x & ~31u);
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t stride = ((static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5) * 32;
+    const int64_t end = __ldg(offsets + S - 1) + __ldg(lengths + S - 1);
+    for (uint64_t g = warp * 32; g < S; g += stride) {
+        const FlatGroup fg = flat_group(keys, bases, lengths, offsets, S, end, g, lane);
+        if (fg.nonempty == 0) continue;
+        // packed: every non-empty stream's output offset minus its position
+        // is the first non-empty stream's offset (its position is 0)
+        const int64_t D0 = __shfl_sync(0xFFFFFFFFu, fg.off, __ffs(fg.nonempty) - 1);
+        const bool packed = __ballot_sync(0xFFFFFFFFu, fg.len > 0 && fg.off - fg.P != D0) == 0u;
+        if (packed && fg.T < (int64_t{1} << 30))
+            run_walk<C>(reinterpret_cast<RunEntry *>(table), fg, out + D0, lane);
         else
-            flat_walk<uint64_t>(table, len > 0 ? static_cast<uint64_t>(P) : 0xC000000000000000ull,
-                                static_cast<uint64_t>(T), lane);
-        __syncwarp();
+            flat_positions(table, fg, out, lane);
     }
 }
 
 // Variants 0-3: tiles (8 or 16 elements per thread, default or streaming
 // stores); 4-8: streams to lanes (32, 8, 16, 4 or 1 lanes per stream);
-// 9: flattened warps.
-constexpr int kBatchVariants = 10;
+// 9: flattened warps; 10, 11: flattened warps with runs of 4 or 8 values.
+constexpr int kBatchVariants = 12;
 const char *kBatchVariantNames[kBatchVariants] = {
-    "st32",          "st32.cs",      "st32x2",       "st32x2.cs", "warp-stream",
-    "lane8-stream", "lane16-stream", "lane4-stream", "lane1-stream", "flat-warp"};
+    "st32",          "st32.cs",      "st32x2",       "st32x2.cs",    "warp-stream", "lane8-stream",
+    "lane16-stream", "lane4-stream", "lane1-stream", "flat-warp", "flat-run4",   "flat-run8"};
 
 size_t batch_smem(int variant, int block) {
     return variant >= 9 ? static_cast<size_t>(block) * sizeof(FlatEntry) : 0;
@@ -431,7 +575,9 @@ const void *batch_fn(int variant) {
         case 6: return reinterpret_cast<const void *>(&batch_stream_kernel<16>);
         case 7: return reinterpret_cast<const void *>(&batch_stream_kernel<4>);
         case 8: return reinterpret_cast<const void *>(&batch_stream_kernel<1>);
-        default: return reinterpret_cast<const void *>(&batch_flat_kernel);
+        case 9: return reinterpret_cast<const void *>(&batch_flat_kernel);
+        case 10: return reinterpret_cast<const void *>(&batch_run_kernel<4>);
+        default: return reinterpret_cast<const void *>(&batch_run_kernel<8>);
     }
 }
 
@@ -461,7 +607,12 @@ cudaError_t launch_batch(const Cfg &cfg, const uint64_t *keys, const uint64_t *b
     const uint32_t S = static_cast<uint32_t>(nstreams);
     if (c.variant >= 9) {
         const size_t smem = batch_smem(c.variant, cfg.block);
-        batch_flat_kernel<<<grid, cfg.block, smem, stream>>>(keys, bases, lengths, offsets, S, out);
+        if (c.variant == 9)
+            batch_flat_kernel<<<grid, cfg.block, smem, stream>>>(keys, bases, lengths, offsets, S, out);
+        else if (c.variant == 10)
+            batch_run_kernel<4><<<grid, cfg.block, smem, stream>>>(keys, bases, lengths, offsets, S, out);
+        else
+            batch_run_kernel<8><<<grid, cfg.block, smem, stream>>>(keys, bases, lengths, offsets, S, out);
         return cudaGetLastError();
     }
     if (c.variant >= 4) {

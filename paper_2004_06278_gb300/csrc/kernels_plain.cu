@@ -14,6 +14,8 @@
 // Nothing is read from memory.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "internal.h"
 #include "squares_device.cuh"
 #include "stores.cuh"
@@ -180,7 +182,9 @@ struct OddPairs {
 
 // Store ceiling: the plain kernels' chunking, grid and store path with no
 // generator arithmetic; every element is the 32-bit value passed in place
-// of the key.
+// of the key, and the counter-base argument carries a pause in nanoseconds
+// that each thread takes after each chunk (paced writers: a store stream
+// that saturates the memory system runs slower than one that leaves gaps).
 struct OpFill {
     static constexpr int kHeadParity = 0;
     using T = uint32_t;
@@ -224,6 +228,15 @@ __device__ __forceinline__ void store_chunk(void *p, const uint32_t (&w)[BYTES /
     }
 }
 
+// After each chunk: a pause for the store-ceiling kernel (ctr0 carries its
+// length in nanoseconds), nothing for the generators.
+template <class Op>
+__device__ __forceinline__ void pace(uint64_t ctr0) {
+    if constexpr (std::is_same<Op, OpFill>::value) {
+        if (ctr0 != 0) __nanosleep(static_cast<unsigned>(ctr0));
+    }
+}
+
 // head: elements [0, head) and tail: [head + nvec*EPV, n) are written one
 // element per thread; the vector region in between by whole chunks.
 template <class Op, int BYTES, bool CS>
@@ -256,6 +269,7 @@ __global__ void __launch_bounds__(512)
         uint32_t w[W];
         Op::template chunk<W>(y, e, key, c2, w);
         store_chunk<BYTES, CS>(p, w);
+        pace<Op>(ctr0);
         y = add64(y, ystep);
         e = add64(e, estep);
         p += pstep;
@@ -324,6 +338,7 @@ __global__ void __launch_bounds__(512)
                          : "memory");
             asm volatile("cp.async.bulk.commit_group;" ::: "memory");
         }
+        pace<Op>(ctr0);
         y = add64(y, ystep);
         e = add64(e, estep);
         gp += gstep;

@@ -113,7 +113,7 @@ def test_fill_argument_checks(lib):
     assert e.value.status == sq.SQ_ERANGE
     sq.sq_debug_fail_next("sq_fill_u32")
     with pytest.raises(sq.SquaresError) as e:
-        sq.sq_fill_u32(7, 16, 0x1000, (1, 256, 0))
+        sq.sq_fill_u32(7, 16, 0x1000, (1, 256, 0), 50)
     assert e.value.status == sq.SQ_ECUDA and "injected" in e.value.message
 
 
@@ -142,7 +142,9 @@ def test_batch_and_fused_argument_checks(lib):
 def test_config_table(lib):
     assert sq.sq_num_variants(sq.SQ_KERNEL_U32) == 7
     assert sq.sq_variant_name(sq.SQ_KERNEL_U32, 6) == "bulk64"
-    assert sq.sq_num_variants(sq.SQ_KERNEL_BATCH) == 10
+    assert sq.sq_num_variants(sq.SQ_KERNEL_BATCH) == 12
+    assert sq.sq_variant_name(sq.SQ_KERNEL_BATCH, 10) == "flat-run4"
+    assert sq.sq_variant_name(sq.SQ_KERNEL_BATCH, 11) == "flat-run8"
     assert sq.sq_variant_name(sq.SQ_KERNEL_BATCH, 4) == "warp-stream"
     assert sq.sq_variant_name(sq.SQ_KERNEL_BATCH, 5) == "lane8-stream"
     assert sq.sq_variant_name(sq.SQ_KERNEL_BATCH, 6) == "lane16-stream"

@@ -163,13 +163,13 @@ def stream_writes(off, ln, LPS, groups):
 
 # --- flattened warps (variant 9) -------------------------------------------
 
-def flat_writes(keys, bases, off, ln, force64=False):
+def flat_writes(keys, bases, off, ln, force64=False, end_override=None):
     """Positions written by batch_flat_kernel, with the Weyl term y the
     kernel forms for each: [(position, stream, index, y)]. force64 takes the
     64-bit position walk whatever the group's total (the kernel takes it
     from 2^31 values on)."""
     S = len(off)
-    end = _s64(off[S - 1] + ln[S - 1])
+    end = _s64(off[S - 1] + ln[S - 1]) if end_override is None else end_override
     out = []
     for g in range(0, S, 32):
         L, O, K, B = [0] * 32, [0] * 32, [0] * 32, [0] * 32
@@ -218,6 +218,90 @@ def flat_writes(keys, bases, off, ln, force64=False):
                     out.append((_s64(dst + p), s, p - ps, (y0 + p * key) & M64))
             before = (before + _popc(starts)) & M32
             b += 32
+    return out
+
+
+# --- flattened warps with runs (variants 10, 11) ---------------------------
+
+def _owner_lane(P, q):
+    """Binary search over the lanes' stream starts, as owner_lane does."""
+    k = 0
+    step = 16
+    while step:
+        if P[k + step] <= q:
+            k += step
+        step >>= 1
+    return k
+
+
+def run_writes(keys, bases, off, ln, C, out_elem=0):
+    """Positions written by batch_run_kernel<C>, with the Weyl term y formed
+    for each: [(position, stream, index, y)]. out_elem is the output
+    pointer's address in elements (its value modulo C places the runs).
+    Groups that are not packed, or hold 2^30 values or more, take the
+    per-position walk (flat_writes on the group alone)."""
+    S = len(off)
+    end = _s64(off[S - 1] + ln[S - 1])
+    out = []
+    for g in range(0, S, 32):
+        L, O, K, B = [0] * 32, [0] * 32, [0] * 32, [0] * 32
+        for lane in range(32):
+            s = g + lane
+            if s < S:
+                L[lane], O[lane], K[lane], B[lane] = ln[s], off[s], keys[s], bases[s]
+            n, o = L[lane], O[lane]
+            if o < 0:
+                n = 0
+            elif n > _s64(end - o):
+                n = _s64(end - o)
+            L[lane] = min(max(n, 0), 1 << 57)
+        P, acc = [], 0
+        for lane in range(32):
+            P.append(acc)
+            acc = _s64(acc + L[lane])
+        T = acc
+        nonempty = [i for i in range(32) if L[i] > 0]
+        if not nonempty:
+            continue
+        D0 = O[nonempty[0]]
+        packed = all(O[i] - P[i] == D0 for i in nonempty)
+        if not packed or T >= (1 << 30):
+            sub = [(s - g) for s in range(g, min(g + 32, S))]
+            # the per-position walk of this group alone, with the batch extent
+            for e, s, i, y in flat_writes([keys[g + x] for x in sub], [bases[g + x] for x in sub],
+                                          [off[g + x] for x in sub], [ln[g + x] for x in sub],
+                                          end_override=end):
+                out.append((e, g + s, i, y))
+            continue
+        E = [P[i] + L[i] for i in range(32)]
+        tab = [((B[i] * K[i]) & M64, K[i], P[i], E[i], _owner_lane(P, E[i])) for i in range(32)]
+        a = (out_elem + D0) % C
+        b = -a
+        while b < T:
+            for lane in range(32):
+                q = b + lane * C
+                qc = 0 if q < 0 else (q if q < T else T - 1)
+                k = _owner_lane(P, qc)
+                if q >= T:
+                    continue
+                ys, key, Pk, stop, nx = tab[k]
+                y = (ys + (q - Pk) * key) & M64
+                cur = k
+                vals = []
+                for i in range(C):
+                    if q + i == stop:
+                        cur = nx
+                        ys, key, Pk, stop, nx = tab[cur]
+                        y = ys
+                    vals.append((q + i, cur, y))
+                    y = (y + key) & M64
+                aligned_run = q >= 0 and q + C <= T
+                if aligned_run:
+                    assert (out_elem + D0 + q) % C == 0, "misaligned vector store"
+                for p, cur, y in vals:
+                    if 0 <= p < T:
+                        out.append((D0 + p, g + cur, p - P[cur], y))
+            b += 32 * C
     return out
 
 
@@ -326,3 +410,53 @@ def test_flat_model_huge_lengths_are_capped():
     keys, bases = [3, 5, 7], [0, 0, 0]
     for e, s, i, _ in flat_writes(keys, bases, off, ln):
         assert 0 <= e < 16
+
+
+@pytest.mark.parametrize("C", [4, 8])
+def test_run_model_valid_batches(C):
+    """Flattened warps with runs: every element written once with its own
+    stream's Weyl term, on packed batches (the run walk) and on batches with
+    gaps (the per-position walk), for every placement of the output pointer
+    modulo the run length; every vector store aligned."""
+    rng = np.random.default_rng(5 + C)
+    for trial in range(300):
+        off, ln, keys, bases = _valid_batch(rng, trial)
+        out_elem = int(rng.integers(0, 64))
+        got = run_writes(keys, bases, off, ln, C, out_elem)
+        positions = [e for e, _, _, _ in got]
+        assert len(positions) == len(set(positions)), trial
+        assert {e: (s, i) for e, s, i, _ in got} == _expected(off, ln), trial
+        for e, s, i, y in got:
+            assert y == ((bases[s] + i) * keys[s]) & M64, (trial, e)
+
+
+@pytest.mark.parametrize("C", [4, 8])
+def test_run_model_packed_batches_take_the_run_walk(C):
+    """The benchmark's short-stream batches are packed (offsets are the
+    exclusive prefix sum of the lengths), so every group takes the run walk:
+    checked on the recipe's length ranges, including empty streams."""
+    rng = np.random.default_rng(11 + C)
+    for trial in range(60):
+        S = int(rng.integers(1, 100))
+        lo, hi = [(3, 30), (30, 300), (1, 4)][trial % 3]
+        ln = [int(x) for x in rng.integers(lo, hi, S)]
+        for s in rng.integers(0, S, 3):
+            ln[int(s)] = 0
+        lead = int(rng.integers(0, 9))
+        off = [int(x) + lead for x in np.concatenate([[0], np.cumsum(ln)[:-1]])]
+        keys = [int(k) | 1 for k in rng.integers(0, 1 << 63, S, dtype=np.uint64)]
+        bases = [int(x) for x in rng.integers(0, 1 << 64, S, dtype=np.uint64)]
+        got = run_writes(keys, bases, off, ln, C, int(rng.integers(0, 16)))
+        assert {e: (s, i) for e, s, i, _ in got} == _expected(off, ln), trial
+        assert len(got) == sum(ln)
+
+
+@pytest.mark.parametrize("C", [4, 8])
+def test_run_model_invalid_metadata_stays_inside_the_extent(C):
+    rng = np.random.default_rng(21 + C)
+    for trial in range(300):
+        off, ln, keys, bases = _invalid_batch(rng, trial % 4)
+        end = off[-1] + ln[-1]
+        for e, s, i, _ in run_writes(keys, bases, off, ln, C, int(rng.integers(0, 16))):
+            assert 0 <= e < end, (trial, e, end)
+            assert off[s] <= e < off[s] + ln[s]

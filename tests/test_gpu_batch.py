@@ -74,6 +74,45 @@ def test_every_launch_config(gpu_lib):
         C.sq_set_config(C.SQ_KERNEL_BATCH, 0, 0, 256, 0)
 
 
+def _packed_batch(S, seed, lo, hi, empty=5, wrap_every=4):
+    """Streams laid end to end (offsets = exclusive prefix sum of the lengths),
+    a few of them empty, every wrap_every-th one wrapping at 2^64."""
+    rng = np.random.default_rng(seed)
+    lengths = rng.integers(lo, hi, S).astype(np.int64)
+    lengths[rng.integers(0, S, empty)] = 0
+    bases = rng.integers(0, 1 << 64, S, dtype=np.uint64)
+    for s in range(0, S, wrap_every):
+        bases[s] = np.uint64((1 << 64) - int(rng.integers(1, max(2, int(lengths[s]) + 1))))
+    offsets = (np.cumsum(lengths) - lengths).astype(np.int64)
+    return workloads.Batch(key_seed=seed, bases=bases, lengths=lengths, offsets=offsets)
+
+
+@pytest.mark.parametrize("lo,hi", [(1, 4), (3, 30), (30, 300), (300, 3000)])
+def test_run_variants_on_packed_batches(gpu_lib, lo, hi):
+    """The flattened-warp run variants (flat-run4, flat-run8) take their run
+    walk on packed batches: every output against the oracle, at every output
+    offset modulo the run length (the runs' vector stores are placed by the
+    output address), in several block sizes; a batch with one gap makes its
+    group take the per-position walk in the same launch."""
+    runs = [v for v in range(C.sq_num_variants(C.SQ_KERNEL_BATCH))
+            if C.sq_variant_name(C.SQ_KERNEL_BATCH, v).startswith("flat-run")]
+    assert len(runs) == 2
+    b = _packed_batch(1000, seed=lo, lo=lo, hi=hi)
+    g = _packed_batch(1000, seed=hi, lo=lo, hi=hi)
+    g.offsets[500:] += 3  # a gap before stream 500: its group is not packed
+    try:
+        for v in runs:
+            for block in (64, 256, 512):
+                C.sq_set_config(C.SQ_KERNEL_BATCH, 0, v, block, 0)
+                for off in range(8):
+                    got, n_out = _run(gpu_lib, b, offset_elems=off, extra=11)
+                    assert np.array_equal(got, _expect(b, n_out)), (v, block, off)
+                got, n_out = _run(gpu_lib, g, offset_elems=block % 5)
+                assert np.array_equal(got, _expect(g, n_out)), (v, block, "gap")
+    finally:
+        C.sq_set_config(C.SQ_KERNEL_BATCH, 0, 0, 256, 0)
+
+
 def test_batch_equals_plain_per_stream(gpu_lib):
     import torch
 

@@ -212,8 +212,8 @@ def test_capture_with_wide_and_bulk_variants(gpu_lib, name):
 def test_fill_store_ceiling_kernel(gpu_lib):
     """sq_fill_u32 (the write-only kernel the benchmark measures the store
     ceiling with) writes exactly [out, out + n) with its value in every
-    store variant and block size, at every 4-byte offset, in device memory
-    and in pinned host memory."""
+    store variant and block size, at every 4-byte offset (one of them with
+    a pause after each chunk), in device memory and in pinned host memory."""
     import torch
 
     n = 2 * 152 * 512 * 16 + 13
@@ -222,13 +222,13 @@ def test_fill_store_ceiling_kernel(gpu_lib):
         for block in (128, 512):
             for off in (0, 1, 3, 7):
                 g = Guarded(n * 4, off * 4)
-                C.sq_fill_u32(value, n, g.ptr, (v, block, 0), stream_handle())
+                C.sq_fill_u32(value, n, g.ptr, (v, block, 0), 100 * (off == 3), stream_handle())
                 assert g.guards_intact(), (v, block, off)
                 assert np.all(g.payload(np.uint32) == value), (v, block, off)
     host = torch.zeros(n + 8, dtype=torch.int32, pin_memory=True)
     for off in (0, 3):
         host.zero_()
-        C.sq_fill_u32(value, n, host[off:].data_ptr(), None, stream_handle())
+        C.sq_fill_u32(value, n, host[off:].data_ptr(), None, 0, stream_handle())
         torch.cuda.synchronize()
         got = host.numpy().view(np.uint32)
         assert np.all(got[off:off + n] == value) and not got[:off].any() and not got[off + n:].any()
