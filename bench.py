@@ -757,11 +757,8 @@ def breakdown(torch, sq, C, workloads, dev, ms32_plain, tuned_from_file=False, w
     fs = torch.empty(S, dtype=torch.int64, device=dev)
     fh = torch.empty(256, dtype=torch.int64, device=dev)
     torch.cuda.synchronize()
-    if not tuned_from_file:
-        # tuned on 2^14 of the streams (2^32 counters), applied to the full size
-        C.sq_autotune(C.SQ_KERNEL_FUSED, (1 << 14) * cps)
-        cf = C.sq_get_config(C.SQ_KERNEL_FUSED, (1 << 14) * cps)
-        C.sq_set_config(C.SQ_KERNEL_FUSED, S * cps, cf.variant, cf.block, cf.ctas_per_sm)
+    # default launch configuration (block 256, as many CTAs as fit): tuning on a
+    # 2^32-counter subset picked 128-thread blocks, 1 % slower at full size
     cfgf = C.sq_get_config(C.SQ_KERNEL_FUSED, S * cps)
     ms = _time_launches(torch, lambda: C.sq_fused_stats(fk.data_ptr(), fb.data_ptr(), S, cps,
                                                         fx.data_ptr(), fs.data_ptr(),
