@@ -236,7 +236,8 @@ typedef struct {
                           * stream to 32, 8, 16, 4 or 1 lanes, 9 lays 32 streams end to
                           * end per warp, 10 and 11 do the same with runs of 4 or 8
                           * consecutive values per lane (4-11 are for many short
-                          * streams) */
+                          * streams); for SQ_KERNEL_FUSED 0 gives each stream part
+                          * to a CTA, 1 to a warp */
     int32_t block;       /* threads per CTA: 128, 256 or 512 (SQ_KERNEL_BATCH also 64) */
     int32_t ctas_per_sm; /* persistent grid = SMs * ctas_per_sm; 0 = max resident */
     int32_t reserved;

@@ -145,6 +145,9 @@ def test_config_table(lib):
     assert sq.sq_num_variants(sq.SQ_KERNEL_BATCH) == 12
     assert sq.sq_variant_name(sq.SQ_KERNEL_BATCH, 10) == "flat-run4"
     assert sq.sq_variant_name(sq.SQ_KERNEL_BATCH, 11) == "flat-run8"
+    assert sq.sq_num_variants(sq.SQ_KERNEL_FUSED) == 2
+    assert sq.sq_variant_name(sq.SQ_KERNEL_FUSED, 0) == "cta-item"
+    assert sq.sq_variant_name(sq.SQ_KERNEL_FUSED, 1) == "warp-item"
     assert sq.sq_variant_name(sq.SQ_KERNEL_BATCH, 4) == "warp-stream"
     assert sq.sq_variant_name(sq.SQ_KERNEL_BATCH, 5) == "lane8-stream"
     assert sq.sq_variant_name(sq.SQ_KERNEL_BATCH, 6) == "lane16-stream"

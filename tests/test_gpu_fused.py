@@ -47,16 +47,35 @@ def test_fused_zero_counters_clears_outputs(gpu_lib):
     assert not x.any() and not s.any() and not h.any()
 
 
+@pytest.mark.parametrize("S,cps", [(1, 5000), (2, (1 << 20) + 3), (700, 1)])
+def test_fused_both_item_layouts(gpu_lib, S, cps):
+    """CTA items (variant 0) and warp items (variant 1) give the oracle's
+    statistics on few long streams (split into many parts) and on many
+    one-counter streams (most threads of a CTA idle)."""
+    rng = np.random.default_rng(S + cps)
+    keys = gpu_lib.make_keys(15, S)
+    bases = rng.integers(0, 1 << 64, S, dtype=np.uint64)
+    ex, es, eh = oracle.fused_stats(oracle.make_keys(15, S), bases, cps)
+    try:
+        for v in (0, 1):
+            C.sq_set_config(C.SQ_KERNEL_FUSED, 0, v, 256, 0)
+            x, s, h = _run(gpu_lib, keys, bases, cps)
+            assert np.array_equal(x, ex) and np.array_equal(s, es) and np.array_equal(h, eh), v
+    finally:
+        C.sq_set_config(C.SQ_KERNEL_FUSED, 0, 0, 256, 0)
+
+
 def test_fused_every_launch_config(gpu_lib):
     S, cps = 300, 5000
     keys = gpu_lib.make_keys(14, S)
     bases = np.arange(S, dtype=np.uint64) * np.uint64(1 << 40)
     ex, es, eh = oracle.fused_stats(oracle.make_keys(14, S), bases, cps)
     try:
-        for block in (128, 256, 512):
-            for ctas in (1, 2, 0):
-                C.sq_set_config(C.SQ_KERNEL_FUSED, 0, 0, block, ctas)
-                x, s, h = _run(gpu_lib, keys, bases, cps)
-                assert np.array_equal(x, ex) and np.array_equal(s, es) and np.array_equal(h, eh)
+        for v in range(C.sq_num_variants(C.SQ_KERNEL_FUSED)):
+            for block in (128, 256, 512):
+                for ctas in (1, 2, 0):
+                    C.sq_set_config(C.SQ_KERNEL_FUSED, 0, v, block, ctas)
+                    x, s, h = _run(gpu_lib, keys, bases, cps)
+                    assert np.array_equal(x, ex) and np.array_equal(s, es) and np.array_equal(h, eh), (v, block, ctas)
     finally:
         C.sq_set_config(C.SQ_KERNEL_FUSED, 0, 0, 256, 0)
