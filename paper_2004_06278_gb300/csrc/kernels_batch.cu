@@ -357,34 +357,45 @@ __device__ __forceinline__ void flat_walk(const FlatEntry *table, Pos Pe, Pos T,
 // more. A clamped length is also capped at 2^57 so that the 64-bit scan
 // cannot overflow; every write then lies inside its owner's clamped range,
 // whatever the metadata.
-// One group of 32 streams of a flattened warp: lane L's stream g + L, its
-// length clamped to the batch extent (0 for a negative offset, at most
-// 2^57), and its first position P in the warp's value sequence (exclusive
-// scan of the lengths; T values in all).
+// Lane L's stream s = g + L of a flattened warp's group: its metadata, with
+// the length clamped to the batch extent (0 for a negative offset or s past
+// the last stream, at most 2^57).
+struct StreamMeta {
+    int64_t len, off;
+    uint64_t key, base;
+};
+
+__device__ __forceinline__ StreamMeta stream_meta(const uint64_t *__restrict__ keys,
+                                                  const uint64_t *__restrict__ bases,
+                                                  const int64_t *__restrict__ lengths,
+                                                  const int64_t *__restrict__ offsets, uint32_t S,
+                                                  int64_t end, uint64_t s) {
+    constexpr int64_t kLenCap = int64_t{1} << 57;
+    StreamMeta m{0, 0, 0, 0};
+    if (s < S) {
+        m.len = __ldg(lengths + s);
+        m.off = __ldg(offsets + s);
+        m.key = __ldg(keys + s);
+        m.base = __ldg(bases + s);
+    }
+    if (m.off < 0) m.len = 0;
+    else if (m.len > end - m.off) m.len = end - m.off;
+    if (m.len < 0) m.len = 0;
+    if (m.len > kLenCap) m.len = kLenCap;
+    return m;
+}
+
+// One group of 32 streams of a flattened warp: lane L's stream and its first
+// position P in the warp's value sequence (exclusive scan of the clamped
+// lengths; T values in all).
 struct FlatGroup {
     int64_t len, off, P, T;
     uint64_t key, base;
     uint32_t nonempty;  // lanes with len > 0
 };
 
-__device__ __forceinline__ FlatGroup flat_group(const uint64_t *__restrict__ keys,
-                                                const uint64_t *__restrict__ bases,
-                                                const int64_t *__restrict__ lengths,
-                                                const int64_t *__restrict__ offsets, uint32_t S,
-                                                int64_t end, uint64_t g, uint32_t lane) {
-    constexpr int64_t kLenCap = int64_t{1} << 57;
-    FlatGroup fg{0, 0, 0, 0, 0, 0, 0};
-    const uint64_t s = g + lane;
-    if (s < S) {
-        fg.len = __ldg(lengths + s);
-        fg.off = __ldg(offsets + s);
-        fg.key = __ldg(keys + s);
-        fg.base = __ldg(bases + s);
-    }
-    if (fg.off < 0) fg.len = 0;
-    else if (fg.len > end - fg.off) fg.len = end - fg.off;
-    if (fg.len < 0) fg.len = 0;
-    if (fg.len > kLenCap) fg.len = kLenCap;
+__device__ __forceinline__ FlatGroup flat_group(const StreamMeta &m, uint32_t lane) {
+    FlatGroup fg{m.len, m.off, 0, 0, m.key, m.base, 0};
     int64_t inc = fg.len;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -428,7 +439,8 @@ __global__ void __launch_bounds__(512)
     const uint64_t stride = ((static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5) * 32;
     const int64_t end = __ldg(offsets + S - 1) + __ldg(lengths + S - 1);
     for (uint64_t g = warp * 32; g < S; g += stride)
-        flat_positions(table, flat_group(keys, bases, lengths, offsets, S, end, g, lane), out, lane);
+        flat_positions(table, flat_group(stream_meta(keys, bases, lengths, offsets, S, end, g + lane), lane), out,
+                       lane);
 }
 
 // Flattened warps with runs (variants 10 and 11, C = 4 or 8), for the same
@@ -539,7 +551,7 @@ __global__ void __launch_bounds__(512)
     const uint64_t stride = ((static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5) * 32;
     const int64_t end = __ldg(offsets + S - 1) + __ldg(lengths + S - 1);
     for (uint64_t g = warp * 32; g < S; g += stride) {
-        const FlatGroup fg = flat_group(keys, bases, lengths, offsets, S, end, g, lane);
+        const FlatGroup fg = flat_group(stream_meta(keys, bases, lengths, offsets, S, end, g + lane), lane);
         if (fg.nonempty == 0) continue;
         // packed: every non-empty stream's output offset minus its position
         // is the first non-empty stream's offset (its position is 0)
@@ -552,13 +564,113 @@ __global__ void __launch_bounds__(512)
     }
 }
 
+// Flattened warps over aligned segments (variants 12-14, C = 4, 8 or 16),
+// for the same batches and any offsets: the output is cut at every C-element
+// boundary of its address (4C bytes), and each stream's outputs into the
+// pieces between those cuts, its segments -- whole aligned C-element blocks,
+// and a shorter piece at a stream's start or end. A warp lays its group's
+// segments end to end (an exclusive scan of the segment counts, one per lane)
+// and walks them 32 per step, one segment per lane: the owner of segment r is
+// the last lane whose first segment is at or before r (empty streams own no
+// segment and are passed over), found by a binary search over the lanes with
+// shuffles; the owner's table entry gives the segment's first Weyl term and
+// address. Every lane generates C consecutive counters of one stream (round
+// 1 squared once, then carried by additions) and stores a whole segment with
+// one aligned vector store, a piece element by element. Nothing is written
+// outside the owner's clamped range. A group holding a stream of 2^26 values
+// or more takes batch_flat_kernel's walk instead, so that segment indexes and
+// in-stream positions stay 32-bit.
+struct alignas(16) SegEntry {
+    uint64_t y;    // Weyl term of the stream's first segment's first element
+    uint64_t key;  //
+    uint64_t dst;  // that element's output address (4C-byte aligned), plus lo
+    uint32_t Q;    // the stream's first segment in the warp's sequence
+    uint32_t hi;   // lo + length: the stream's end, in elements from dst
+};
+static_assert(sizeof(SegEntry) == sizeof(FlatEntry), "segment and flat tables share the warp's slots");
+
+constexpr int64_t kSegLenCap = int64_t{1} << 26;
+
+// The group's segment walk. The stream's first output lies lo elements past
+// a C-element boundary of the address (off + a, a = the output's own
+// distance past one), so its outputs are elements lo .. hi - 1 of the
+// segments that start at dst.
+template <int C>
+__device__ __forceinline__ void seg_walk(SegEntry *tab, const StreamMeta &m, uint32_t a,
+                                         uint32_t *__restrict__ out, uint32_t lane) {
+    const uint32_t lo = static_cast<uint32_t>((static_cast<uint64_t>(m.off) + a) % C);
+    const uint32_t hi = lo + static_cast<uint32_t>(m.len);
+    const uint32_t nseg = m.len > 0 ? (hi + C - 1) / C : 0u;
+    uint32_t inc = nseg;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+        if (lane >= static_cast<uint32_t>(d)) inc += o;
+    }
+    const uint32_t Q = inc - nseg;
+    const uint32_t R = __shfl_sync(0xFFFFFFFFu, inc, 31);
+    if (m.len > 0)
+        tab[lane] = SegEntry{(m.base - lo) * m.key, m.key,
+                             (reinterpret_cast<uint64_t>(out) + (static_cast<uint64_t>(m.off) - lo) * 4u) | lo, Q, hi};
+    __syncwarp();
+    for (uint32_t b = 0; b < R; b += 32) {
+        const uint32_t r = b + lane;
+        const uint32_t k = owner_lane(Q, r < R ? r : R - 1);
+        if (r < R) {
+            const SegEntry e = tab[k];
+            const uint32_t v = (r - e.Q) * C;  // the segment's first element, from dst
+            const uint32_t first = static_cast<uint32_t>(e.dst) & (C - 1u);
+            uint32_t *p = reinterpret_cast<uint32_t *>(e.dst - first) + v;
+            const uint64_t y = e.y + static_cast<uint64_t>(v) * e.key;
+            uint32_t w[C];
+            run32<C>(y, round1_delta(y, e.key), e.key, (e.key * e.key) << 1, w);
+            if (v >= first && v + C <= e.hi) {
+                if constexpr (C == 4) {
+                    store16B<false>(p, w[0], w[1], w[2], w[3]);
+                } else {
+                    store32B<false>(p, *reinterpret_cast<const uint32_t(*)[8]>(&w[0]));
+                    if constexpr (C == 16) store32B<false>(p + 8, *reinterpret_cast<const uint32_t(*)[8]>(&w[8]));
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < C; ++i)
+                    if (v + i >= first && v + i < e.hi) p[i] = w[i];
+            }
+        }
+    }
+    __syncwarp();
+}
+
+template <int C>
+__global__ void __launch_bounds__(512)
+    batch_seg_kernel(const uint64_t *__restrict__ keys, const uint64_t *__restrict__ bases,
+                     const int64_t *__restrict__ lengths, const int64_t *__restrict__ offsets,
+                     uint32_t S, uint32_t *__restrict__ out) {
+    extern __shared__ FlatEntry flat_tables[];
+    FlatEntry *table = flat_tables + (threadIdx.x & ~31u);
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t stride = ((static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5) * 32;
+    const int64_t end = __ldg(offsets + S - 1) + __ldg(lengths + S - 1);
+    const uint32_t a = static_cast<uint32_t>((reinterpret_cast<uintptr_t>(out) >> 2) % C);
+    for (uint64_t g = warp * 32; g < S; g += stride) {
+        const StreamMeta m = stream_meta(keys, bases, lengths, offsets, S, end, g + lane);
+        if (__any_sync(0xFFFFFFFFu, m.len >= kSegLenCap))
+            flat_positions(table, flat_group(m, lane), out, lane);
+        else
+            seg_walk<C>(reinterpret_cast<SegEntry *>(table), m, a, out, lane);
+    }
+}
+
 // Variants 0-3: tiles (8 or 16 elements per thread, default or streaming
 // stores); 4-8: streams to lanes (32, 8, 16, 4 or 1 lanes per stream);
-// 9: flattened warps; 10, 11: flattened warps with runs of 4 or 8 values.
-constexpr int kBatchVariants = 12;
+// 9: flattened warps; 10, 11: flattened warps with runs of 4 or 8 values;
+// 12-14: flattened warps over aligned segments of 4, 8 or 16 values.
+constexpr int kBatchVariants = 15;
 const char *kBatchVariantNames[kBatchVariants] = {
     "st32",          "st32.cs",      "st32x2",       "st32x2.cs",    "warp-stream", "lane8-stream",
-    "lane16-stream", "lane4-stream", "lane1-stream", "flat-warp", "flat-run4",   "flat-run8"};
+    "lane16-stream", "lane4-stream", "lane1-stream", "flat-warp", "flat-run4",   "flat-run8",
+    "flat-seg4",     "flat-seg8",    "flat-seg16"};
 
 size_t batch_smem(int variant, int block) {
     return variant >= 9 ? static_cast<size_t>(block) * sizeof(FlatEntry) : 0;
@@ -577,7 +689,10 @@ const void *batch_fn(int variant) {
         case 8: return reinterpret_cast<const void *>(&batch_stream_kernel<1>);
         case 9: return reinterpret_cast<const void *>(&batch_flat_kernel);
         case 10: return reinterpret_cast<const void *>(&batch_run_kernel<4>);
-        default: return reinterpret_cast<const void *>(&batch_run_kernel<8>);
+        case 11: return reinterpret_cast<const void *>(&batch_run_kernel<8>);
+        case 12: return reinterpret_cast<const void *>(&batch_seg_kernel<4>);
+        case 13: return reinterpret_cast<const void *>(&batch_seg_kernel<8>);
+        default: return reinterpret_cast<const void *>(&batch_seg_kernel<16>);
     }
 }
 
@@ -611,8 +726,14 @@ cudaError_t launch_batch(const Cfg &cfg, const uint64_t *keys, const uint64_t *b
             batch_flat_kernel<<<grid, cfg.block, smem, stream>>>(keys, bases, lengths, offsets, S, out);
         else if (c.variant == 10)
             batch_run_kernel<4><<<grid, cfg.block, smem, stream>>>(keys, bases, lengths, offsets, S, out);
-        else
+        else if (c.variant == 11)
             batch_run_kernel<8><<<grid, cfg.block, smem, stream>>>(keys, bases, lengths, offsets, S, out);
+        else if (c.variant == 12)
+            batch_seg_kernel<4><<<grid, cfg.block, smem, stream>>>(keys, bases, lengths, offsets, S, out);
+        else if (c.variant == 13)
+            batch_seg_kernel<8><<<grid, cfg.block, smem, stream>>>(keys, bases, lengths, offsets, S, out);
+        else
+            batch_seg_kernel<16><<<grid, cfg.block, smem, stream>>>(keys, bases, lengths, offsets, S, out);
         return cudaGetLastError();
     }
     if (c.variant >= 4) {

@@ -18,7 +18,9 @@ must be written exactly once, at offsets[s] + i; on metadata that breaks
 them (unsorted or overlapping streams, negative offsets, an early stream
 far past the last one's end) every write must stay inside the extent
 [0, offsets[S-1] + lengths[S-1]) and no position may be written twice by
-the tile kernel. The models are kept in step with the CUDA code by hand.
+the tile kernel. The models are kept in step with the CUDA code by hand; the run
+(variants 10, 11) and segment (variants 12-14) walks have models of their
+own below.
 """
 import numpy as np
 import pytest
@@ -305,6 +307,72 @@ def run_writes(keys, bases, off, ln, C, out_elem=0):
     return out
 
 
+# --- flattened warps over aligned segments (variants 12-14) ---------------
+
+SEG_LEN_CAP = 1 << 26
+
+
+def seg_writes(keys, bases, off, ln, C, out_elem=0, cap=SEG_LEN_CAP):
+    """Positions written by batch_seg_kernel<C>, with the Weyl term y formed
+    for each: [(position, stream, index, y)]. out_elem is the output
+    pointer's address in elements (its value modulo C places the segment
+    cuts). A group with a clamped length of `cap` or more takes the
+    per-position walk (flat_writes on the group alone); the kernel's cap is
+    2^26, smaller ones exercise the switch on small batches."""
+    S = len(off)
+    end = _s64(off[S - 1] + ln[S - 1])
+    a = out_elem % C
+    out = []
+    for g in range(0, S, 32):
+        L, O, K, B = [0] * 32, [0] * 32, [0] * 32, [0] * 32
+        for lane in range(32):
+            s = g + lane
+            if s < S:
+                L[lane], O[lane], K[lane], B[lane] = ln[s], off[s], keys[s], bases[s]
+            n, o = L[lane], O[lane]
+            if o < 0:
+                n = 0
+            elif n > _s64(end - o):
+                n = _s64(end - o)
+            L[lane] = min(max(n, 0), 1 << 57)
+        if any(x >= cap for x in L):
+            sub = range(g, min(g + 32, S))
+            for e, s, i, y in flat_writes([keys[x] for x in sub], [bases[x] for x in sub],
+                                          [off[x] for x in sub], [ln[x] for x in sub],
+                                          end_override=end):
+                out.append((e, g + s, i, y))
+            continue
+        lo = [((O[i] & M64) + a) % C for i in range(32)]
+        hi = [lo[i] + L[i] for i in range(32)]
+        assert all(h < (1 << 32) for h in hi)
+        nseg = [(hi[i] + C - 1) // C if L[i] > 0 else 0 for i in range(32)]
+        Q, acc = [], 0
+        for i in range(32):
+            Q.append(acc)
+            acc += nseg[i]
+        R = acc
+        assert R < (1 << 32)
+        tab = [(((B[i] - lo[i]) * K[i]) & M64, K[i], O[i] - lo[i], lo[i], Q[i], hi[i]) if L[i] > 0 else None
+               for i in range(32)]
+        for b in range(0, R, 32):
+            for lane in range(32):
+                r = b + lane
+                k = _owner_lane(Q, min(r, R - 1))
+                if r >= R:
+                    continue
+                assert tab[k] is not None, ("empty owner", r)
+                Y, key, dst, first, Qk, h = tab[k]
+                v = (r - Qk) * C
+                assert 0 <= v < h, ("segment outside its stream", r)
+                whole = v >= first and v + C <= h
+                if whole:
+                    assert (out_elem + dst + v) % C == 0, "misaligned vector store"
+                for i in range(C):
+                    if first <= v + i < h:
+                        out.append((dst + v + i, g + k, v + i - first, (Y + (v + i) * key) & M64))
+    return out
+
+
 # --- batches ---------------------------------------------------------------
 
 def _valid_batch(rng, trial):
@@ -460,3 +528,72 @@ def test_run_model_invalid_metadata_stays_inside_the_extent(C):
         for e, s, i, _ in run_writes(keys, bases, off, ln, C, int(rng.integers(0, 16))):
             assert 0 <= e < end, (trial, e, end)
             assert off[s] <= e < off[s] + ln[s]
+
+
+SEG_CS = [4, 8, 16]
+
+
+@pytest.mark.parametrize("C", SEG_CS)
+def test_seg_model_valid_batches(C):
+    """Flattened warps over aligned segments: every element written once
+    with its own stream's Weyl term, on batches with and without gaps, for
+    every placement of the output pointer modulo C; every whole segment's
+    vector store aligned."""
+    rng = np.random.default_rng(31 + C)
+    for trial in range(300):
+        off, ln, keys, bases = _valid_batch(rng, trial)
+        out_elem = int(rng.integers(0, 64))
+        got = seg_writes(keys, bases, off, ln, C, out_elem)
+        positions = [e for e, _, _, _ in got]
+        assert len(positions) == len(set(positions)), trial
+        assert {e: (s, i) for e, s, i, _ in got} == _expected(off, ln), trial
+        for e, s, i, y in got:
+            assert y == ((bases[s] + i) * keys[s]) & M64, (trial, e)
+
+
+@pytest.mark.parametrize("C", SEG_CS)
+def test_seg_model_recipe_batches(C):
+    """The benchmark's short-stream length ranges (packed, with empty
+    streams), and the switch to the per-position walk for a group holding a
+    stream at or above the length cap (a small cap in the model)."""
+    rng = np.random.default_rng(41 + C)
+    for trial in range(60):
+        S = int(rng.integers(1, 100))
+        lo, hi = [(3, 30), (30, 300), (1, 4)][trial % 3]
+        ln = [int(x) for x in rng.integers(lo, hi, S)]
+        for s in rng.integers(0, S, 3):
+            ln[int(s)] = 0
+        lead = int(rng.integers(0, 9))
+        off = [int(x) + lead for x in np.concatenate([[0], np.cumsum(ln)[:-1]])]
+        keys = [int(k) | 1 for k in rng.integers(0, 1 << 63, S, dtype=np.uint64)]
+        bases = [int(x) for x in rng.integers(0, 1 << 64, S, dtype=np.uint64)]
+        for cap in (SEG_LEN_CAP, hi // 2):
+            got = seg_writes(keys, bases, off, ln, C, int(rng.integers(0, 32)), cap=cap)
+            assert {e: (s, i) for e, s, i, _ in got} == _expected(off, ln), (trial, cap)
+            assert len(got) == sum(ln)
+            for e, s, i, y in got:
+                assert y == ((bases[s] + i) * keys[s]) & M64, (trial, e)
+
+
+@pytest.mark.parametrize("C", SEG_CS)
+def test_seg_model_invalid_metadata_stays_inside_the_extent(C):
+    rng = np.random.default_rng(51 + C)
+    for trial in range(300):
+        off, ln, keys, bases = _invalid_batch(rng, trial % 4)
+        end = off[-1] + ln[-1]
+        for e, s, i, _ in seg_writes(keys, bases, off, ln, C, int(rng.integers(0, 32)),
+                                     cap=int(rng.choice([SEG_LEN_CAP, 200]))):
+            assert 0 <= e < end, (trial, e, end)
+            assert off[s] <= e < off[s] + ln[s]
+
+
+@pytest.mark.parametrize("C", SEG_CS)
+def test_seg_index_widths(C):
+    """Below the cap every segment index, segment count and in-stream
+    element index of a group fits the kernel's 32-bit arithmetic: 32 streams
+    of 2^26 - 1 values, each starting C - 1 elements past a cut."""
+    hi = (C - 1) + SEG_LEN_CAP - 1
+    nseg = (hi + C - 1) // C
+    assert hi < (1 << 32)
+    assert 32 * nseg + 31 < (1 << 32)
+    assert (nseg - 1) * C + C - 1 < (1 << 32)

@@ -113,6 +113,51 @@ def test_run_variants_on_packed_batches(gpu_lib, lo, hi):
         C.sq_set_config(C.SQ_KERNEL_BATCH, 0, 0, 256, 0)
 
 
+def _seg_variants():
+    segs = [v for v in range(C.sq_num_variants(C.SQ_KERNEL_BATCH))
+            if C.sq_variant_name(C.SQ_KERNEL_BATCH, v).startswith("flat-seg")]
+    assert len(segs) == 3
+    return segs
+
+
+@pytest.mark.parametrize("lo,hi", [(1, 4), (3, 30), (30, 300), (300, 3000)])
+def test_seg_variants_on_batches(gpu_lib, lo, hi):
+    """The flattened-warp segment variants (flat-seg4, -seg8, -seg16) need
+    no packing: every output against the oracle on a packed batch at every
+    output offset modulo 16 (the segment cuts follow the output address),
+    and on a batch with gaps, in several block sizes."""
+    b = _packed_batch(1000, seed=lo + 7, lo=lo, hi=hi)
+    g = workloads.small_ragged_batch(1000, seed=hi + 7, max_len=hi, gap_max=5)
+    g.lengths[::97] = 0
+    try:
+        for v in _seg_variants():
+            for block in (64, 256, 512):
+                C.sq_set_config(C.SQ_KERNEL_BATCH, 0, v, block, 0)
+                for off in range(16):
+                    got, n_out = _run(gpu_lib, b, offset_elems=off, extra=11)
+                    assert np.array_equal(got, _expect(b, n_out)), (v, block, off)
+                got, n_out = _run(gpu_lib, g, offset_elems=block % 5)
+                assert np.array_equal(got, _expect(g, n_out)), (v, block, "gaps")
+    finally:
+        C.sq_set_config(C.SQ_KERNEL_BATCH, 0, 0, 256, 0)
+
+
+def test_seg_variants_long_stream_group(gpu_lib):
+    """A group holding a stream of 2^26 values or more takes the
+    per-position walk, the next group the segment walk, in one launch."""
+    b = _packed_batch(40, seed=99, lo=1, hi=200, empty=2)
+    b.lengths[5] = (1 << 26) + 3
+    b.offsets = (np.cumsum(b.lengths) - b.lengths).astype(np.int64)
+    want = _expect(b, b.total + 11)
+    try:
+        for v in _seg_variants():
+            C.sq_set_config(C.SQ_KERNEL_BATCH, 0, v, 256, 0)
+            got, n_out = _run(gpu_lib, b, offset_elems=3, extra=11)
+            assert np.array_equal(got, want), v
+    finally:
+        C.sq_set_config(C.SQ_KERNEL_BATCH, 0, 0, 256, 0)
+
+
 def test_batch_equals_plain_per_stream(gpu_lib):
     import torch
 
