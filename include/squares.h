@@ -234,12 +234,15 @@ typedef struct {
     int32_t variant;     /* kernel body: store width / cache policy, see sq_variant_name;
                           * for SQ_KERNEL_BATCH 0-3 tile the packed output, 4-8 give each
                           * stream to 32, 8, 16, 4 or 1 lanes, 9 lays 32 streams end to
-                          * end per warp, 10 and 11 do the same with runs of 4 or 8
-                          * consecutive values per lane (4-11 are for many short
-                          * streams); for SQ_KERNEL_FUSED 0 gives each stream part
-                          * to a CTA, 1 to a warp */
+                          * end per warp, one position per lane, 10-12 give each lane
+                          * an aligned segment of 4, 8 or 16 values of one of a warp's
+                          * 32 streams (4-12 are for many short streams); for
+                          * SQ_KERNEL_FUSED 0 gives each stream part to a CTA, 1 to a
+                          * warp */
     int32_t block;       /* threads per CTA: 128, 256 or 512 (SQ_KERNEL_BATCH also 64) */
-    int32_t ctas_per_sm; /* persistent grid = SMs * ctas_per_sm; 0 = max resident */
+    int32_t ctas_per_sm; /* persistent grid = SMs * ctas_per_sm; 0 = max resident, except
+                          * for the SQ_KERNEL_BATCH flattened-warp variants (9-12),
+                          * where 0 launches one warp per 32 streams */
     int32_t reserved;
 } sq_launch_config;
 
@@ -269,7 +272,7 @@ int sq_autotune(int kernel_id, size_t n_hint);
  * uses for batches in the same stream-count bucket (floor(log2(nstreams))).
  * The streams-to-lanes and flattened-warp variants are candidates
  * only when the mean stream length (read back from the batch extent) is at
- * most 8192, and a variant whose probe (block 256, as many CTAs as fit)
+ * most 8192, and a variant whose probe (block 256, ctas_per_sm 0)
  * takes over 3x the best time so far is not timed in its other
  * configurations. sq_autotune(SQ_KERNEL_BATCH, n) times the tile variants
  * only. Synchronous; allocates no device memory; must not run during stream

@@ -664,9 +664,10 @@ int sq_autotune_batch(const uint64_t *keys, const uint64_t *ctr_bases, const int
     // streams-to-lanes and flattened-warp variants (4 and up) are candidates
     // only for streams of at most 8192 values on average: on longer ones a
     // lane group or a warp walks a whole stream alone and cannot win. Each
-    // variant is first timed at block 256 with as many CTAs as fit; if that
-    // takes over 3x the best time so far, its other configurations are not
-    // timed.
+    // variant is first timed at block 256 with ctas_per_sm 0 (as many CTAs
+    // as fit; one warp per 32 streams for the flattened-warp variants); if
+    // that takes over 3x the best time so far, its other configurations are
+    // not timed.
     int64_t last_off = 0, last_len = 0;
     e = cudaMemcpy(&last_off, offsets + nstreams - 1, sizeof(int64_t), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess)
@@ -688,7 +689,7 @@ int sq_autotune_batch(const uint64_t *keys, const uint64_t *ctr_bases, const int
         }, ms);
     };
     for (int v = 0; v < nv && e == cudaSuccess; ++v) {
-        // probe: block 256, as many CTAs as fit
+        // probe: block 256, ctas_per_sm 0
         const sq::Cfg probe{v, 256, 0};
         float ms = 0.f;
         e = time_cfg(probe, &ms);

@@ -17,8 +17,8 @@
 // no write lands outside it, whatever the other streams' offsets. There are
 // no spin-waits and no inter-CTA communication. Batches of many short
 // streams are better served by the streams-to-lanes kernels (variants 4-8)
-// and the flattened-warp kernel (variant 9) further down, which the batch
-// autotuner picks when they win.
+// and the flattened-warp kernels (variants 9-12) further down, which the
+// batch autotuner picks when they win.
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -443,202 +443,150 @@ __global__ void __launch_bounds__(512)
                        lane);
 }
 
-// Flattened warps with runs (variants 10 and 11, C = 4 or 8), for the same
-// batches: the group's 32 streams are laid end to end as in batch_flat_kernel,
-// but each lane takes a run of C consecutive positions per step (the warp
-// 32 * C), so the owner is looked up once per run and consecutive values of
-// a stream follow by Weyl addition (y += key), as in the plain kernels.
-// Where the group's streams are packed (each non-empty stream's output
-// starts where the previous one's ends, as an exclusive prefix sum of the
-// lengths gives), position p's output is dst[p] for one dst, and the runs
-// are placed so that each run is one aligned C * 4-byte vector store; a run
-// that reaches before position 0 or past the group's end is stored element
-// by element. A group with gaps or overlaps between its streams, or with
-// 2^30 values or more, takes batch_flat_kernel's walk instead, so every
-// write stays inside its owner's clamped range whatever the metadata.
+// Flattened warps over aligned segments (variants 10-12, C = 4, 8 or 16),
+// for the same batches and any offsets. The output is cut at every C-element
+// boundary of its address (4C bytes); a stream's outputs fall into whole
+// segments (aligned blocks of C outputs of the stream) and at most two
+// pieces (the shorter runs at its start and end, or one run when the stream
+// lies inside one block). A warp takes 32 streams at a time, in two passes:
 //
-// Run walk: the warp's stream starts P (one per lane, non-decreasing, P of
-// lane 0 is 0) give the owner of a position q as the last lane L with
-// P_L <= q (empty streams share the next stream's start and are passed
-// over), found by a binary search over the lanes with shuffles. The table
-// holds, per lane, the stream's Weyl term at its first position (ctr_base *
-// key), its key, its first and end positions and the lane that owns its
-// end position; a run that reaches the end of its stream continues with
-// that entry.
-struct alignas(16) RunEntry {
-    uint64_t ys;
-    uint64_t key;
-    uint32_t P;
-    uint32_t E;
-    uint32_t nxt;
-    uint32_t pad;
-};
-static_assert(sizeof(RunEntry) == sizeof(FlatEntry), "run and flat tables share the warp's slots");
+// * Whole segments. The streams' whole segments are laid end to end (an
+//   exclusive scan of the counts, one per lane) and walked 32 per step, one
+//   segment per lane, owner found as in flat_walk (one bit per stream start
+//   in the step, a warp OR and a population count) over a table of the
+//   streams that have whole segments. The table holds each stream's Weyl
+//   term, round-1 step and output address at its first whole segment, and
+//   the per-segment strides, so segment j of the stream starts from
+//   y + j * (C * key), e + j * (C * c2) and dst + j * C: every lane generates
+//   C consecutive counters of one stream (round 1 squared once, then carried
+//   by additions) and writes them with one aligned vector store.
+// * Pieces. Each lane writes its own stream's pieces, element by element:
+//   C counters from the piece's block start, stored where they fall inside
+//   the stream.
+//
+// The key differs from lane to lane, so round 1's step is carried by
+// accumulation (t += e, e += c2: additions only) rather than by the
+// launch-uniform j * c2 terms the plain kernels use. Nothing is written
+// outside the owner's clamped range. A group holding a stream of 2^26
+// values or more takes batch_flat_kernel's walk instead, so that segment
+// counts and in-stream positions stay 32-bit.
 
-// Last lane L with P_L <= q, given the lanes' non-decreasing P and P_0 <= q.
-__device__ __forceinline__ uint32_t owner_lane(uint32_t P, uint32_t q) {
-    uint32_t k = 0;
-#pragma unroll
-    for (uint32_t step = 16; step > 0; step >>= 1) {
-        const uint32_t pc = __shfl_sync(0xFFFFFFFFu, P, k + step);
-        if (pc <= q) k += step;
-    }
-    return k;
-}
-
+// squares32 of C consecutive counters of one key from y, e = t(ctr+1) -
+// t(ctr) and c2 = 2*key^2, round 1 carried by two additions per counter.
 template <int C>
-__device__ __forceinline__ void run_walk(RunEntry *tab, const FlatGroup &fg, uint32_t *__restrict__ dst,
-                                         uint32_t lane) {
-    const int32_t T = static_cast<int32_t>(fg.T);
-    const uint32_t P = static_cast<uint32_t>(fg.P);
-    const uint32_t E = P + static_cast<uint32_t>(fg.len);
-    tab[lane] = RunEntry{fg.base * fg.key, fg.key, P, E, owner_lane(P, E), 0u};
-    __syncwarp();
-    // dst[0] lies `a` elements past a C * 4-byte boundary: runs start at
-    // positions -a + C * j, so that every run's vector store is aligned.
-    const int32_t a = static_cast<int32_t>((reinterpret_cast<uintptr_t>(dst) >> 2) % C);
-    for (int32_t b = -a; b < T; b += 32 * C) {
-        const int32_t q = b + static_cast<int32_t>(lane) * C;
-        const uint32_t qc = q < 0 ? 0u : static_cast<uint32_t>(q < T ? q : T - 1);
-        const uint32_t k = owner_lane(P, qc);
-        if (q < T) {
-            const RunEntry e = tab[k];
-            uint64_t y = e.ys + static_cast<uint64_t>(static_cast<int64_t>(q) - static_cast<int64_t>(e.P)) * e.key;
-            uint64_t key = e.key;
-            int32_t stop = static_cast<int32_t>(e.E);
-            uint32_t nx = e.nxt;
-            uint32_t w[C];
+__device__ __forceinline__ void run32_lane(uint64_t y, uint64_t e, uint64_t key, uint64_t c2, uint32_t (&w)[C]) {
+    uint64_t t = round1_value(y);
 #pragma unroll
-            for (int i = 0; i < C; ++i) {
-                // At the end of the stream, the next non-empty one starts with
-                // its first value. (At the group's end, T, the entry taken is
-                // some lane's and the values past T are not stored.)
-                if (q + i == stop) {
-                    const RunEntry f = tab[nx];
-                    y = f.ys;
-                    key = f.key;
-                    stop = static_cast<int32_t>(f.E);
-                    nx = f.nxt;
-                }
-                const uint64_t z = add64(y, key);
-                w[i] = squares32_yz(y, z);
-                y = z;
-            }
-            if (q >= 0 && q + C <= T) {
-                if constexpr (C == 8)
-                    store32B<false>(dst + q, w);
-                else
-                    store16B<false>(dst + q, w[0], w[1], w[2], w[3]);
-            } else {
-#pragma unroll
-                for (int i = 0; i < C; ++i)
-                    if (q + i >= 0 && q + i < T) dst[q + i] = w[i];
-            }
-        }
-    }
-    __syncwarp();
-}
-
-template <int C>
-__global__ void __launch_bounds__(512)
-    batch_run_kernel(const uint64_t *__restrict__ keys, const uint64_t *__restrict__ bases,
-                     const int64_t *__restrict__ lengths, const int64_t *__restrict__ offsets,
-                     uint32_t S, uint32_t *__restrict__ out) {
-    extern __shared__ FlatEntry flat_tables[];
-    FlatEntry *table = flat_tables + (threadIdx.x & ~31u);
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t stride = ((static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5) * 32;
-    const int64_t end = __ldg(offsets + S - 1) + __ldg(lengths + S - 1);
-    for (uint64_t g = warp * 32; g < S; g += stride) {
-        const FlatGroup fg = flat_group(stream_meta(keys, bases, lengths, offsets, S, end, g + lane), lane);
-        if (fg.nonempty == 0) continue;
-        // packed: every non-empty stream's output offset minus its position
-        // is the first non-empty stream's offset (its position is 0)
-        const int64_t D0 = __shfl_sync(0xFFFFFFFFu, fg.off, __ffs(fg.nonempty) - 1);
-        const bool packed = __ballot_sync(0xFFFFFFFFu, fg.len > 0 && fg.off - fg.P != D0) == 0u;
-        if (packed && fg.T < (int64_t{1} << 30))
-            run_walk<C>(reinterpret_cast<RunEntry *>(table), fg, out + D0, lane);
-        else
-            flat_positions(table, fg, out, lane);
+    for (int j = 0; j < C; ++j) {
+        const uint64_t z = add64(y, key);
+        w[j] = squares32_tyz(t, y, z);
+        y = z;
+        t = add64(t, e);
+        e = add64(e, c2);
     }
 }
 
-// Flattened warps over aligned segments (variants 12-14, C = 4, 8 or 16),
-// for the same batches and any offsets: the output is cut at every C-element
-// boundary of its address (4C bytes), and each stream's outputs into the
-// pieces between those cuts, its segments -- whole aligned C-element blocks,
-// and a shorter piece at a stream's start or end. A warp lays its group's
-// segments end to end (an exclusive scan of the segment counts, one per lane)
-// and walks them 32 per step, one segment per lane: the owner of segment r is
-// the last lane whose first segment is at or before r (empty streams own no
-// segment and are passed over), found by a binary search over the lanes with
-// shuffles; the owner's table entry gives the segment's first Weyl term and
-// address. Every lane generates C consecutive counters of one stream (round
-// 1 squared once, then carried by additions) and stores a whole segment with
-// one aligned vector store, a piece element by element. Nothing is written
-// outside the owner's clamped range. A group holding a stream of 2^26 values
-// or more takes batch_flat_kernel's walk instead, so that segment indexes and
-// in-stream positions stay 32-bit.
+// One stream of a warp's whole-segment table: at its first whole segment the
+// Weyl term y, the round-1 step e and the output address dst (4C-byte
+// aligned); key and c2 = 2*key^2; the strides of one segment, C*key and
+// C*c2; Q, the stream's first whole segment in the warp's sequence.
 struct alignas(16) SegEntry {
-    uint64_t y;    // Weyl term of the stream's first segment's first element
-    uint64_t key;  //
-    uint64_t dst;  // that element's output address (4C-byte aligned), plus lo
-    uint32_t Q;    // the stream's first segment in the warp's sequence
-    uint32_t hi;   // lo + length: the stream's end, in elements from dst
+    uint64_t y, key, e, c2, kc, c2c, dst;
+    uint32_t Q, pad;
 };
-static_assert(sizeof(SegEntry) == sizeof(FlatEntry), "segment and flat tables share the warp's slots");
+static_assert(sizeof(SegEntry) >= sizeof(FlatEntry), "the flat walk's table fits a segment table's slots");
 
 constexpr int64_t kSegLenCap = int64_t{1} << 26;
 
-// The group's segment walk. The stream's first output lies lo elements past
-// a C-element boundary of the address (off + a, a = the output's own
-// distance past one), so its outputs are elements lo .. hi - 1 of the
-// segments that start at dst.
 template <int C>
-__device__ __forceinline__ void seg_walk(SegEntry *tab, const StreamMeta &m, uint32_t a,
-                                         uint32_t *__restrict__ out, uint32_t lane) {
-    const uint32_t lo = static_cast<uint32_t>((static_cast<uint64_t>(m.off) + a) % C);
-    const uint32_t hi = lo + static_cast<uint32_t>(m.len);
-    const uint32_t nseg = m.len > 0 ? (hi + C - 1) / C : 0u;
-    uint32_t inc = nseg;
+__device__ __forceinline__ void seg_store(uint32_t *p, const uint32_t (&w)[C]) {
+    if constexpr (C == 4) {
+        store16B<false>(p, w[0], w[1], w[2], w[3]);
+    } else {
+        store32B<false>(p, *reinterpret_cast<const uint32_t(*)[8]>(&w[0]));
+        if constexpr (C == 16) store32B<false>(p + 8, *reinterpret_cast<const uint32_t(*)[8]>(&w[8]));
+    }
+}
+
+// The whole-segment pass. The stream's first output lies lo elements past a
+// block start; its outputs are elements lo .. hi - 1 counted from there, and
+// its whole segments the blocks ws .. we - 1 (ws = 1 if lo > 0, we = hi / C).
+template <int C, int LC>
+__device__ __forceinline__ void seg_whole(SegEntry *tab, const StreamMeta &m, uint32_t lo, uint32_t hi,
+                                          uint32_t *__restrict__ out, uint32_t lane) {
+    const uint32_t le = 0xFFFFFFFFu >> (31u - lane);
+    const uint32_t ws = lo != 0u;
+    const uint32_t we = hi >> LC;
+    const uint32_t nw = (m.len > 0 && we > ws) ? we - ws : 0u;
+    uint32_t inc = nw;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, inc, d);
         if (lane >= static_cast<uint32_t>(d)) inc += o;
     }
-    const uint32_t Q = inc - nseg;
+    const uint32_t Q = inc - nw;
     const uint32_t R = __shfl_sync(0xFFFFFFFFu, inc, 31);
-    if (m.len > 0)
-        tab[lane] = SegEntry{(m.base - lo) * m.key, m.key,
-                             (reinterpret_cast<uint64_t>(out) + (static_cast<uint64_t>(m.off) - lo) * 4u) | lo, Q, hi};
-    __syncwarp();
-    for (uint32_t b = 0; b < R; b += 32) {
-        const uint32_t r = b + lane;
-        const uint32_t k = owner_lane(Q, r < R ? r : R - 1);
-        if (r < R) {
-            const SegEntry e = tab[k];
-            const uint32_t v = (r - e.Q) * C;  // the segment's first element, from dst
-            const uint32_t first = static_cast<uint32_t>(e.dst) & (C - 1u);
-            uint32_t *p = reinterpret_cast<uint32_t *>(e.dst - first) + v;
-            const uint64_t y = e.y + static_cast<uint64_t>(v) * e.key;
-            uint32_t w[C];
-            run32<C>(y, round1_delta(y, e.key), e.key, (e.key * e.key) << 1, w);
-            if (v >= first && v + C <= e.hi) {
-                if constexpr (C == 4) {
-                    store16B<false>(p, w[0], w[1], w[2], w[3]);
-                } else {
-                    store32B<false>(p, *reinterpret_cast<const uint32_t(*)[8]>(&w[0]));
-                    if constexpr (C == 16) store32B<false>(p + 8, *reinterpret_cast<const uint32_t(*)[8]>(&w[8]));
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < C; ++i)
-                    if (v + i >= first && v + i < e.hi) p[i] = w[i];
-            }
-        }
+    const uint32_t with = __ballot_sync(0xFFFFFFFFu, nw > 0u);
+    if (nw > 0u) {
+        const uint64_t K = m.key;
+        const uint64_t first = (static_cast<uint64_t>(ws) << LC) - lo;  // first whole element, from the stream's
+        const uint64_t y = (m.base + first) * K;
+        const uint64_t c2 = (K * K) << 1;
+        tab[__popc(with & (le >> 1))] =
+            SegEntry{y, K, round1_delta(y, K), c2, K << LC, c2 << LC,
+                     reinterpret_cast<uint64_t>(out) + (static_cast<uint64_t>(m.off) + first) * 4u, Q, 0u};
     }
     __syncwarp();
+    // Streams without whole segments set no bit: their start never falls in
+    // a window (R < 2^30 below the 0xC0000000 sentinel).
+    const uint32_t Pe = nw > 0u ? Q : 0xC0000000u;
+    uint32_t before = 0xFFFFFFFFu;  // table entries started before the step, minus 1
+    for (uint32_t b = 0; b < R; b += 32) {
+        const uint32_t starts = __reduce_or_sync(0xFFFFFFFFu, window_bit(Pe - b));
+        const uint32_t k = before + __popc(starts & le);
+        before += __popc(starts);
+        const uint32_t r = b + lane;
+        if (r < R) {
+            const SegEntry &e = tab[k];
+            const uint32_t j = r - e.Q;
+            uint32_t w[C];
+            run32_lane<C>(e.y + static_cast<uint64_t>(j) * e.kc, e.e + static_cast<uint64_t>(j) * e.c2c, e.key, e.c2,
+                          w);
+            seg_store<C>(reinterpret_cast<uint32_t *>(e.dst) + (static_cast<size_t>(j) << LC), w);
+        }
+    }
+}
+
+// The pieces pass: block 0 when the stream starts inside it or ends before
+// its end (elements lo .. min(hi, C) - 1), and the last block nseg - 1 when
+// it is another block and the stream ends inside it (elements (nseg-1)*C ..
+// hi - 1). Each is C counters from the block start, stored element by
+// element where they fall inside the stream.
+template <int C, int LC>
+__device__ __forceinline__ void seg_pieces(const StreamMeta &m, uint32_t lo, uint32_t hi,
+                                           uint32_t *__restrict__ out) {
+    const bool has = m.len > 0;
+    const uint32_t nseg = (hi + C - 1) >> LC;
+    const bool head = has && (lo != 0u || hi < static_cast<uint32_t>(C));
+    const bool tail = has && (hi & (C - 1)) != 0u && nseg > 1u;
+#pragma unroll 1
+    for (int piece = 0; piece < 2; ++piece) {
+        if (piece == 0 ? head : tail) {
+            const uint32_t b0 = piece == 0 ? 0u : (nseg - 1u) << LC;  // block start, from the block origin
+            const uint32_t p_lo = piece == 0 ? lo : b0;
+            const uint32_t p_hi = hi < b0 + C ? hi : b0 + C;
+            const uint64_t K = m.key;
+            const uint64_t y = (m.base - lo + b0) * K;
+            uint32_t w[C];
+            run32_lane<C>(y, round1_delta(y, K), K, (K * K) << 1, w);
+            // the block's first output, before out + off when lo > off
+            uint32_t *p = reinterpret_cast<uint32_t *>(reinterpret_cast<uint64_t>(out) +
+                                                       (static_cast<uint64_t>(m.off) - lo + b0) * 4u);
+#pragma unroll
+            for (int i = 0; i < C; ++i)
+                if (b0 + i >= p_lo && b0 + i < p_hi) p[i] = w[i];
+        }
+    }
 }
 
 template <int C>
@@ -646,34 +594,43 @@ __global__ void __launch_bounds__(512)
     batch_seg_kernel(const uint64_t *__restrict__ keys, const uint64_t *__restrict__ bases,
                      const int64_t *__restrict__ lengths, const int64_t *__restrict__ offsets,
                      uint32_t S, uint32_t *__restrict__ out) {
-    extern __shared__ FlatEntry flat_tables[];
-    FlatEntry *table = flat_tables + (threadIdx.x & ~31u);
+    constexpr int LC = C == 4 ? 2 : C == 8 ? 3 : 4;
+    static_assert(C == 1 << LC, "C is 4, 8 or 16");
+    extern __shared__ SegEntry seg_tables[];
+    SegEntry *tab = seg_tables + (threadIdx.x & ~31u);
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const uint64_t stride = ((static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5) * 32;
     const int64_t end = __ldg(offsets + S - 1) + __ldg(lengths + S - 1);
-    const uint32_t a = static_cast<uint32_t>((reinterpret_cast<uintptr_t>(out) >> 2) % C);
+    // the output's distance past a C-element boundary of its address
+    const uint32_t a = static_cast<uint32_t>((reinterpret_cast<uintptr_t>(out) >> 2) & (C - 1));
     for (uint64_t g = warp * 32; g < S; g += stride) {
         const StreamMeta m = stream_meta(keys, bases, lengths, offsets, S, end, g + lane);
-        if (__any_sync(0xFFFFFFFFu, m.len >= kSegLenCap))
-            flat_positions(table, flat_group(m, lane), out, lane);
-        else
-            seg_walk<C>(reinterpret_cast<SegEntry *>(table), m, a, out, lane);
+        if (__any_sync(0xFFFFFFFFu, m.len >= kSegLenCap)) {
+            flat_positions(reinterpret_cast<FlatEntry *>(tab), flat_group(m, lane), out, lane);
+            continue;
+        }
+        const uint32_t lo = static_cast<uint32_t>((static_cast<uint64_t>(m.off) + a) & (C - 1));
+        const uint32_t hi = lo + static_cast<uint32_t>(m.len);
+        seg_whole<C, LC>(tab, m, lo, hi, out, lane);
+        seg_pieces<C, LC>(m, lo, hi, out);
+        __syncwarp();  // the table is rewritten for the next group
     }
 }
 
 // Variants 0-3: tiles (8 or 16 elements per thread, default or streaming
 // stores); 4-8: streams to lanes (32, 8, 16, 4 or 1 lanes per stream);
-// 9: flattened warps; 10, 11: flattened warps with runs of 4 or 8 values;
-// 12-14: flattened warps over aligned segments of 4, 8 or 16 values.
-constexpr int kBatchVariants = 15;
+// 9: flattened warps, one position per lane; 10-12: flattened warps over
+// aligned segments of 4, 8 or 16 values.
+constexpr int kBatchVariants = 13;
 const char *kBatchVariantNames[kBatchVariants] = {
     "st32",          "st32.cs",      "st32x2",       "st32x2.cs",    "warp-stream", "lane8-stream",
-    "lane16-stream", "lane4-stream", "lane1-stream", "flat-warp", "flat-run4",   "flat-run8",
-    "flat-seg4",     "flat-seg8",    "flat-seg16"};
+    "lane16-stream", "lane4-stream", "lane1-stream", "flat-warp",    "flat-seg4",   "flat-seg8",
+    "flat-seg16"};
 
 size_t batch_smem(int variant, int block) {
-    return variant >= 9 ? static_cast<size_t>(block) * sizeof(FlatEntry) : 0;
+    if (variant == 9) return static_cast<size_t>(block) * sizeof(FlatEntry);
+    return variant >= 10 ? static_cast<size_t>(block) * sizeof(SegEntry) : 0;
 }
 
 const void *batch_fn(int variant) {
@@ -688,10 +645,8 @@ const void *batch_fn(int variant) {
         case 7: return reinterpret_cast<const void *>(&batch_stream_kernel<4>);
         case 8: return reinterpret_cast<const void *>(&batch_stream_kernel<1>);
         case 9: return reinterpret_cast<const void *>(&batch_flat_kernel);
-        case 10: return reinterpret_cast<const void *>(&batch_run_kernel<4>);
-        case 11: return reinterpret_cast<const void *>(&batch_run_kernel<8>);
-        case 12: return reinterpret_cast<const void *>(&batch_seg_kernel<4>);
-        case 13: return reinterpret_cast<const void *>(&batch_seg_kernel<8>);
+        case 10: return reinterpret_cast<const void *>(&batch_seg_kernel<4>);
+        case 11: return reinterpret_cast<const void *>(&batch_seg_kernel<8>);
         default: return reinterpret_cast<const void *>(&batch_seg_kernel<16>);
     }
 }
@@ -721,19 +676,20 @@ cudaError_t launch_batch(const Cfg &cfg, const uint64_t *keys, const uint64_t *b
     const uint32_t head = static_cast<uint32_t>(((32 - (addr % 32)) % 32) / 4);
     const uint32_t S = static_cast<uint32_t>(nstreams);
     if (c.variant >= 9) {
-        const size_t smem = batch_smem(c.variant, cfg.block);
+        // Flattened warps: with ctas_per_sm = 0, one group of 32 streams per
+        // warp (the block scheduler balances groups of unequal work);
+        // otherwise a persistent grid of ctas_per_sm CTAs per SM.
+        const uint64_t groups_grid = (static_cast<uint64_t>(S) + c.block - 1) / c.block;
+        const unsigned fgrid = c.ctas_per_sm > 0 ? grid : static_cast<unsigned>(groups_grid);
+        const size_t smem = batch_smem(c.variant, c.block);
         if (c.variant == 9)
-            batch_flat_kernel<<<grid, cfg.block, smem, stream>>>(keys, bases, lengths, offsets, S, out);
+            batch_flat_kernel<<<fgrid, c.block, smem, stream>>>(keys, bases, lengths, offsets, S, out);
         else if (c.variant == 10)
-            batch_run_kernel<4><<<grid, cfg.block, smem, stream>>>(keys, bases, lengths, offsets, S, out);
+            batch_seg_kernel<4><<<fgrid, c.block, smem, stream>>>(keys, bases, lengths, offsets, S, out);
         else if (c.variant == 11)
-            batch_run_kernel<8><<<grid, cfg.block, smem, stream>>>(keys, bases, lengths, offsets, S, out);
-        else if (c.variant == 12)
-            batch_seg_kernel<4><<<grid, cfg.block, smem, stream>>>(keys, bases, lengths, offsets, S, out);
-        else if (c.variant == 13)
-            batch_seg_kernel<8><<<grid, cfg.block, smem, stream>>>(keys, bases, lengths, offsets, S, out);
+            batch_seg_kernel<8><<<fgrid, c.block, smem, stream>>>(keys, bases, lengths, offsets, S, out);
         else
-            batch_seg_kernel<16><<<grid, cfg.block, smem, stream>>>(keys, bases, lengths, offsets, S, out);
+            batch_seg_kernel<16><<<fgrid, c.block, smem, stream>>>(keys, bases, lengths, offsets, S, out);
         return cudaGetLastError();
     }
     if (c.variant >= 4) {

@@ -142,10 +142,9 @@ def test_batch_and_fused_argument_checks(lib):
 def test_config_table(lib):
     assert sq.sq_num_variants(sq.SQ_KERNEL_U32) == 7
     assert sq.sq_variant_name(sq.SQ_KERNEL_U32, 6) == "bulk64"
-    assert sq.sq_num_variants(sq.SQ_KERNEL_BATCH) == 15
-    assert sq.sq_variant_name(sq.SQ_KERNEL_BATCH, 10) == "flat-run4"
-    assert sq.sq_variant_name(sq.SQ_KERNEL_BATCH, 11) == "flat-run8"
-    assert [sq.sq_variant_name(sq.SQ_KERNEL_BATCH, v) for v in (12, 13, 14)] == [
+    assert sq.sq_num_variants(sq.SQ_KERNEL_BATCH) == 13
+    assert sq.sq_variant_name(sq.SQ_KERNEL_BATCH, 9) == "flat-warp"
+    assert [sq.sq_variant_name(sq.SQ_KERNEL_BATCH, v) for v in (10, 11, 12)] == [
         "flat-seg4", "flat-seg8", "flat-seg16"]
     assert sq.sq_num_variants(sq.SQ_KERNEL_FUSED) == 2
     assert sq.sq_variant_name(sq.SQ_KERNEL_FUSED, 0) == "cta-item"

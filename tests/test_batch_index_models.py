@@ -18,9 +18,8 @@ must be written exactly once, at offsets[s] + i; on metadata that breaks
 them (unsorted or overlapping streams, negative offsets, an early stream
 far past the last one's end) every write must stay inside the extent
 [0, offsets[S-1] + lengths[S-1]) and no position may be written twice by
-the tile kernel. The models are kept in step with the CUDA code by hand; the run
-(variants 10, 11) and segment (variants 12-14) walks have models of their
-own below.
+the tile kernel. The models are kept in step with the CUDA code by hand; the segment
+walk (variants 10-12) has a model of its own below.
 """
 import numpy as np
 import pytest
@@ -223,118 +222,42 @@ def flat_writes(keys, bases, off, ln, force64=False, end_override=None):
     return out
 
 
-# --- flattened warps with runs (variants 10, 11) ---------------------------
-
-def _owner_lane(P, q):
-    """Binary search over the lanes' stream starts, as owner_lane does."""
-    k = 0
-    step = 16
-    while step:
-        if P[k + step] <= q:
-            k += step
-        step >>= 1
-    return k
-
-
-def run_writes(keys, bases, off, ln, C, out_elem=0):
-    """Positions written by batch_run_kernel<C>, with the Weyl term y formed
-    for each: [(position, stream, index, y)]. out_elem is the output
-    pointer's address in elements (its value modulo C places the runs).
-    Groups that are not packed, or hold 2^30 values or more, take the
-    per-position walk (flat_writes on the group alone)."""
-    S = len(off)
-    end = _s64(off[S - 1] + ln[S - 1])
-    out = []
-    for g in range(0, S, 32):
-        L, O, K, B = [0] * 32, [0] * 32, [0] * 32, [0] * 32
-        for lane in range(32):
-            s = g + lane
-            if s < S:
-                L[lane], O[lane], K[lane], B[lane] = ln[s], off[s], keys[s], bases[s]
-            n, o = L[lane], O[lane]
-            if o < 0:
-                n = 0
-            elif n > _s64(end - o):
-                n = _s64(end - o)
-            L[lane] = min(max(n, 0), 1 << 57)
-        P, acc = [], 0
-        for lane in range(32):
-            P.append(acc)
-            acc = _s64(acc + L[lane])
-        T = acc
-        nonempty = [i for i in range(32) if L[i] > 0]
-        if not nonempty:
-            continue
-        D0 = O[nonempty[0]]
-        packed = all(O[i] - P[i] == D0 for i in nonempty)
-        if not packed or T >= (1 << 30):
-            sub = [(s - g) for s in range(g, min(g + 32, S))]
-            # the per-position walk of this group alone, with the batch extent
-            for e, s, i, y in flat_writes([keys[g + x] for x in sub], [bases[g + x] for x in sub],
-                                          [off[g + x] for x in sub], [ln[g + x] for x in sub],
-                                          end_override=end):
-                out.append((e, g + s, i, y))
-            continue
-        E = [P[i] + L[i] for i in range(32)]
-        tab = [((B[i] * K[i]) & M64, K[i], P[i], E[i], _owner_lane(P, E[i])) for i in range(32)]
-        a = (out_elem + D0) % C
-        b = -a
-        while b < T:
-            for lane in range(32):
-                q = b + lane * C
-                qc = 0 if q < 0 else (q if q < T else T - 1)
-                k = _owner_lane(P, qc)
-                if q >= T:
-                    continue
-                ys, key, Pk, stop, nx = tab[k]
-                y = (ys + (q - Pk) * key) & M64
-                cur = k
-                vals = []
-                for i in range(C):
-                    if q + i == stop:
-                        cur = nx
-                        ys, key, Pk, stop, nx = tab[cur]
-                        y = ys
-                    vals.append((q + i, cur, y))
-                    y = (y + key) & M64
-                aligned_run = q >= 0 and q + C <= T
-                if aligned_run:
-                    assert (out_elem + D0 + q) % C == 0, "misaligned vector store"
-                for p, cur, y in vals:
-                    if 0 <= p < T:
-                        out.append((D0 + p, g + cur, p - P[cur], y))
-            b += 32 * C
-    return out
-
-
-# --- flattened warps over aligned segments (variants 12-14) ---------------
+# --- flattened warps over aligned segments (variants 10-12) ---------------
 
 SEG_LEN_CAP = 1 << 26
+
+
+def _clamped_group(keys, bases, off, ln, g, end):
+    S = len(off)
+    L, O, K, B = [0] * 32, [0] * 32, [0] * 32, [0] * 32
+    for lane in range(32):
+        s = g + lane
+        if s < S:
+            L[lane], O[lane], K[lane], B[lane] = ln[s], off[s], keys[s], bases[s]
+        n, o = L[lane], O[lane]
+        if o < 0:
+            n = 0
+        elif n > _s64(end - o):
+            n = _s64(end - o)
+        L[lane] = min(max(n, 0), 1 << 57)
+    return L, O, K, B
 
 
 def seg_writes(keys, bases, off, ln, C, out_elem=0, cap=SEG_LEN_CAP):
     """Positions written by batch_seg_kernel<C>, with the Weyl term y formed
     for each: [(position, stream, index, y)]. out_elem is the output
-    pointer's address in elements (its value modulo C places the segment
+    pointer's address in elements (its value modulo C places the block
     cuts). A group with a clamped length of `cap` or more takes the
     per-position walk (flat_writes on the group alone); the kernel's cap is
-    2^26, smaller ones exercise the switch on small batches."""
+    2^26, smaller ones exercise the switch on small batches. Follows the two
+    passes: whole segments (scan, compacted table, window-bit owner, strides
+    of one segment) and each lane's pieces."""
     S = len(off)
     end = _s64(off[S - 1] + ln[S - 1])
     a = out_elem % C
     out = []
     for g in range(0, S, 32):
-        L, O, K, B = [0] * 32, [0] * 32, [0] * 32, [0] * 32
-        for lane in range(32):
-            s = g + lane
-            if s < S:
-                L[lane], O[lane], K[lane], B[lane] = ln[s], off[s], keys[s], bases[s]
-            n, o = L[lane], O[lane]
-            if o < 0:
-                n = 0
-            elif n > _s64(end - o):
-                n = _s64(end - o)
-            L[lane] = min(max(n, 0), 1 << 57)
+        L, O, K, B = _clamped_group(keys, bases, off, ln, g, end)
         if any(x >= cap for x in L):
             sub = range(g, min(g + 32, S))
             for e, s, i, y in flat_writes([keys[x] for x in sub], [bases[x] for x in sub],
@@ -345,31 +268,64 @@ def seg_writes(keys, bases, off, ln, C, out_elem=0, cap=SEG_LEN_CAP):
         lo = [((O[i] & M64) + a) % C for i in range(32)]
         hi = [lo[i] + L[i] for i in range(32)]
         assert all(h < (1 << 32) for h in hi)
-        nseg = [(hi[i] + C - 1) // C if L[i] > 0 else 0 for i in range(32)]
+        # whole segments
+        ws = [1 if lo[i] else 0 for i in range(32)]
+        we = [hi[i] // C for i in range(32)]
+        nw = [we[i] - ws[i] if L[i] > 0 and we[i] > ws[i] else 0 for i in range(32)]
         Q, acc = [], 0
         for i in range(32):
             Q.append(acc)
-            acc += nseg[i]
+            acc += nw[i]
         R = acc
-        assert R < (1 << 32)
-        tab = [(((B[i] - lo[i]) * K[i]) & M64, K[i], O[i] - lo[i], lo[i], Q[i], hi[i]) if L[i] > 0 else None
-               for i in range(32)]
+        assert R < (1 << 30)
+        with_ = [i for i in range(32) if nw[i] > 0]
+        tab = []
+        for i in with_:
+            first = ws[i] * C - lo[i]
+            y = ((B[i] + first) * K[i]) & M64
+            tab.append((y, K[i], O[i] + first, Q[i], g + i, first))
+        Pe = [Q[i] if nw[i] > 0 else 0xC0000000 for i in range(32)]
+        before = M32
         for b in range(0, R, 32):
-            for lane in range(32):
-                r = b + lane
-                k = _owner_lane(Q, min(r, R - 1))
+            starts = 0
+            for i in range(32):
+                r = (Pe[i] - b) & M32
+                if r < 32:
+                    starts |= 1 << r
+            for t in range(32):
+                k = (before + _popc(starts & (M32 >> (31 - t)))) & M32
+                r = b + t
                 if r >= R:
                     continue
-                assert tab[k] is not None, ("empty owner", r)
-                Y, key, dst, first, Qk, h = tab[k]
-                v = (r - Qk) * C
-                assert 0 <= v < h, ("segment outside its stream", r)
-                whole = v >= first and v + C <= h
-                if whole:
-                    assert (out_elem + dst + v) % C == 0, "misaligned vector store"
+                assert k < len(tab), ("no owner", r)
+                y0, key, dst, Qk, s, first = tab[k]
+                j = r - Qk
+                assert 0 <= j, ("owner after the segment", r)
+                p0 = dst + j * C
+                assert (out_elem + p0) % C == 0, "misaligned vector store"
                 for i in range(C):
-                    if first <= v + i < h:
-                        out.append((dst + v + i, g + k, v + i - first, (Y + (v + i) * key) & M64))
+                    idx = first + j * C + i
+                    assert idx < L[s - g], ("whole segment past the stream", r)
+                    out.append((p0 + i, s, idx, (y0 + (j * C + i) * key) & M64))
+            before = (before + _popc(starts)) & M32
+        # pieces, one lane per stream
+        for i in range(32):
+            if L[i] <= 0:
+                continue
+            nseg = (hi[i] + C - 1) // C
+            head = lo[i] != 0 or hi[i] < C
+            tail = hi[i] % C != 0 and nseg > 1
+            for piece, act in ((0, head), (1, tail)):
+                if not act:
+                    continue
+                b0 = 0 if piece == 0 else (nseg - 1) * C
+                p_lo = lo[i] if piece == 0 else b0
+                p_hi = min(hi[i], b0 + C)
+                y = ((B[i] - lo[i] + b0) * K[i]) & M64
+                for c in range(C):
+                    if p_lo <= b0 + c < p_hi:
+                        idx = b0 + c - lo[i]
+                        out.append((O[i] + idx, g + i, idx, (y + c * K[i]) & M64))
     return out
 
 
@@ -480,56 +436,6 @@ def test_flat_model_huge_lengths_are_capped():
         assert 0 <= e < 16
 
 
-@pytest.mark.parametrize("C", [4, 8])
-def test_run_model_valid_batches(C):
-    """Flattened warps with runs: every element written once with its own
-    stream's Weyl term, on packed batches (the run walk) and on batches with
-    gaps (the per-position walk), for every placement of the output pointer
-    modulo the run length; every vector store aligned."""
-    rng = np.random.default_rng(5 + C)
-    for trial in range(300):
-        off, ln, keys, bases = _valid_batch(rng, trial)
-        out_elem = int(rng.integers(0, 64))
-        got = run_writes(keys, bases, off, ln, C, out_elem)
-        positions = [e for e, _, _, _ in got]
-        assert len(positions) == len(set(positions)), trial
-        assert {e: (s, i) for e, s, i, _ in got} == _expected(off, ln), trial
-        for e, s, i, y in got:
-            assert y == ((bases[s] + i) * keys[s]) & M64, (trial, e)
-
-
-@pytest.mark.parametrize("C", [4, 8])
-def test_run_model_packed_batches_take_the_run_walk(C):
-    """The benchmark's short-stream batches are packed (offsets are the
-    exclusive prefix sum of the lengths), so every group takes the run walk:
-    checked on the recipe's length ranges, including empty streams."""
-    rng = np.random.default_rng(11 + C)
-    for trial in range(60):
-        S = int(rng.integers(1, 100))
-        lo, hi = [(3, 30), (30, 300), (1, 4)][trial % 3]
-        ln = [int(x) for x in rng.integers(lo, hi, S)]
-        for s in rng.integers(0, S, 3):
-            ln[int(s)] = 0
-        lead = int(rng.integers(0, 9))
-        off = [int(x) + lead for x in np.concatenate([[0], np.cumsum(ln)[:-1]])]
-        keys = [int(k) | 1 for k in rng.integers(0, 1 << 63, S, dtype=np.uint64)]
-        bases = [int(x) for x in rng.integers(0, 1 << 64, S, dtype=np.uint64)]
-        got = run_writes(keys, bases, off, ln, C, int(rng.integers(0, 16)))
-        assert {e: (s, i) for e, s, i, _ in got} == _expected(off, ln), trial
-        assert len(got) == sum(ln)
-
-
-@pytest.mark.parametrize("C", [4, 8])
-def test_run_model_invalid_metadata_stays_inside_the_extent(C):
-    rng = np.random.default_rng(21 + C)
-    for trial in range(300):
-        off, ln, keys, bases = _invalid_batch(rng, trial % 4)
-        end = off[-1] + ln[-1]
-        for e, s, i, _ in run_writes(keys, bases, off, ln, C, int(rng.integers(0, 16))):
-            assert 0 <= e < end, (trial, e, end)
-            assert off[s] <= e < off[s] + ln[s]
-
-
 SEG_CS = [4, 8, 16]
 
 
@@ -589,11 +495,15 @@ def test_seg_model_invalid_metadata_stays_inside_the_extent(C):
 
 @pytest.mark.parametrize("C", SEG_CS)
 def test_seg_index_widths(C):
-    """Below the cap every segment index, segment count and in-stream
-    element index of a group fits the kernel's 32-bit arithmetic: 32 streams
-    of 2^26 - 1 values, each starting C - 1 elements past a cut."""
+    """Below the cap every whole-segment index and count of a group, and every
+    in-stream element index, fits the kernel's 32-bit arithmetic, and the
+    total stays below the 0xC0000000 sentinel that streams without whole
+    segments take: 32 streams of 2^26 - 1 values, each starting C - 1
+    elements past a cut."""
     hi = (C - 1) + SEG_LEN_CAP - 1
-    nseg = (hi + C - 1) // C
+    nw = hi // C - 1
+    R = 32 * nw
     assert hi < (1 << 32)
-    assert 32 * nseg + 31 < (1 << 32)
-    assert (nseg - 1) * C + C - 1 < (1 << 32)
+    assert R + 31 < (1 << 30)
+    assert 0xC0000000 - R > 32
+    assert (nw - 1) * C + C - 1 < (1 << 32)

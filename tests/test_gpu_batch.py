@@ -87,32 +87,6 @@ def _packed_batch(S, seed, lo, hi, empty=5, wrap_every=4):
     return workloads.Batch(key_seed=seed, bases=bases, lengths=lengths, offsets=offsets)
 
 
-@pytest.mark.parametrize("lo,hi", [(1, 4), (3, 30), (30, 300), (300, 3000)])
-def test_run_variants_on_packed_batches(gpu_lib, lo, hi):
-    """The flattened-warp run variants (flat-run4, flat-run8) take their run
-    walk on packed batches: every output against the oracle, at every output
-    offset modulo the run length (the runs' vector stores are placed by the
-    output address), in several block sizes; a batch with one gap makes its
-    group take the per-position walk in the same launch."""
-    runs = [v for v in range(C.sq_num_variants(C.SQ_KERNEL_BATCH))
-            if C.sq_variant_name(C.SQ_KERNEL_BATCH, v).startswith("flat-run")]
-    assert len(runs) == 2
-    b = _packed_batch(1000, seed=lo, lo=lo, hi=hi)
-    g = _packed_batch(1000, seed=hi, lo=lo, hi=hi)
-    g.offsets[500:] += 3  # a gap before stream 500: its group is not packed
-    try:
-        for v in runs:
-            for block in (64, 256, 512):
-                C.sq_set_config(C.SQ_KERNEL_BATCH, 0, v, block, 0)
-                for off in range(8):
-                    got, n_out = _run(gpu_lib, b, offset_elems=off, extra=11)
-                    assert np.array_equal(got, _expect(b, n_out)), (v, block, off)
-                got, n_out = _run(gpu_lib, g, offset_elems=block % 5)
-                assert np.array_equal(got, _expect(g, n_out)), (v, block, "gap")
-    finally:
-        C.sq_set_config(C.SQ_KERNEL_BATCH, 0, 0, 256, 0)
-
-
 def _seg_variants():
     segs = [v for v in range(C.sq_num_variants(C.SQ_KERNEL_BATCH))
             if C.sq_variant_name(C.SQ_KERNEL_BATCH, v).startswith("flat-seg")]
@@ -125,19 +99,21 @@ def test_seg_variants_on_batches(gpu_lib, lo, hi):
     """The flattened-warp segment variants (flat-seg4, -seg8, -seg16) need
     no packing: every output against the oracle on a packed batch at every
     output offset modulo 16 (the segment cuts follow the output address),
-    and on a batch with gaps, in several block sizes."""
+    and on a batch with gaps, in several block sizes, with one warp per 32
+    streams (ctas_per_sm 0) and with a persistent grid (1 CTA per SM)."""
     b = _packed_batch(1000, seed=lo + 7, lo=lo, hi=hi)
     g = workloads.small_ragged_batch(1000, seed=hi + 7, max_len=hi, gap_max=5)
     g.lengths[::97] = 0
     try:
         for v in _seg_variants():
             for block in (64, 256, 512):
-                C.sq_set_config(C.SQ_KERNEL_BATCH, 0, v, block, 0)
-                for off in range(16):
-                    got, n_out = _run(gpu_lib, b, offset_elems=off, extra=11)
-                    assert np.array_equal(got, _expect(b, n_out)), (v, block, off)
-                got, n_out = _run(gpu_lib, g, offset_elems=block % 5)
-                assert np.array_equal(got, _expect(g, n_out)), (v, block, "gaps")
+                for ctas in (0, 1):
+                    C.sq_set_config(C.SQ_KERNEL_BATCH, 0, v, block, ctas)
+                    for off in range(16):
+                        got, n_out = _run(gpu_lib, b, offset_elems=off, extra=11)
+                        assert np.array_equal(got, _expect(b, n_out)), (v, block, ctas, off)
+                    got, n_out = _run(gpu_lib, g, offset_elems=block % 5)
+                    assert np.array_equal(got, _expect(g, n_out)), (v, block, ctas, "gaps")
     finally:
         C.sq_set_config(C.SQ_KERNEL_BATCH, 0, 0, 256, 0)
 
