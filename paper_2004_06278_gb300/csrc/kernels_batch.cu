@@ -394,16 +394,30 @@ struct FlatGroup {
     uint32_t nonempty;  // lanes with len > 0
 };
 
+// The scan runs in 32-bit words when every length is below 2^26 (so that
+// the 32 lengths sum below 2^31), else in 64-bit words.
 __device__ __forceinline__ FlatGroup flat_group(const StreamMeta &m, uint32_t lane) {
     FlatGroup fg{m.len, m.off, 0, 0, m.key, m.base, 0};
-    int64_t inc = fg.len;
+    if (__any_sync(0xFFFFFFFFu, fg.len >= (int64_t{1} << 26))) {
+        int64_t inc = fg.len;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int64_t o = __shfl_up_sync(0xFFFFFFFFu, inc, d);
-        if (lane >= static_cast<uint32_t>(d)) inc += o;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t o = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+            if (lane >= static_cast<uint32_t>(d)) inc += o;
+        }
+        fg.P = inc - fg.len;
+        fg.T = __shfl_sync(0xFFFFFFFFu, inc, 31);
+    } else {
+        const uint32_t len = static_cast<uint32_t>(fg.len);
+        uint32_t inc = len;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+            if (lane >= static_cast<uint32_t>(d)) inc += o;
+        }
+        fg.P = static_cast<int64_t>(inc - len);
+        fg.T = static_cast<int64_t>(__shfl_sync(0xFFFFFFFFu, inc, 31));
     }
-    fg.P = inc - fg.len;
-    fg.T = __shfl_sync(0xFFFFFFFFu, inc, 31);
     fg.nonempty = __ballot_sync(0xFFFFFFFFu, fg.len > 0);
     return fg;
 }
