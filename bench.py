@@ -73,6 +73,8 @@ def parse_args():
     p.add_argument("--profile-n", type=int, default=1 << 28)
     p.add_argument("--profile-variant", help="batch variant name for the batch_* profile cases "
                                              "(default: the one named in the case)")
+    p.add_argument("--profile-block", type=int, default=0,
+                   help="block size for the batch_* profile cases (default: the tuner's pick)")
     p.add_argument("--reference-budget-s", type=float, default=60.0,
                    help="wall time the reference arm aims to spend on its K steps")
     return p.parse_args()
@@ -977,11 +979,12 @@ def profile_case(args):
     #                block 512, as many CTAs per SM as fit;
     #   batch_tiny:  2^22 streams, [3, 30) (mean ~11): the same.
     regimes = {"batch_mid": (1 << 14, 3e3, 3e4, "st32.cs", 128),
-               "batch_short": (1 << 20, 30, 300, "flat-warp", 512),
-               "batch_tiny": (1 << 22, 3, 30, "flat-warp", 512)}
+               "batch_short": (1 << 20, 30, 300, "flat-seg8", 64),
+               "batch_tiny": (1 << 22, 3, 30, "flat-warp", 128)}
     if args.profile in regimes:
         S, lo, hi, vname, block = regimes[args.profile]
         vname = args.profile_variant or vname
+        block = args.profile_block or block
         bt = workloads.ragged_batch(S, seed=7, lo=lo, hi=hi)
         k = torch.from_numpy(sq.make_keys(7, bt.nstreams).view(np.int64)).to(dev)
         bb = torch.from_numpy(bt.bases.view(np.int64)).to(dev)
