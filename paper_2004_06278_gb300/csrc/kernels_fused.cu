@@ -2,12 +2,8 @@
 //
 // Work is split into items (stream s, part p). Variant 0 gives an item to a
 // whole CTA: every thread walks a contiguous run of the item's counters by
-// Weyl addition, and since the stream index derives from the block index
-// alone, the key and the round-1 recurrence constants are the same in every
-// thread of the block (the compiler keeps them in uniform registers), which
-// lets the loop take 16 counters per block of the recurrence. Variant 1
-// gives an item to a warp (per-thread copies of the constants, blocks of
-// 8). In both, the top-byte histogram is kept per warp in shared memory and
+// Weyl addition, round 1 carried by accumulation (walk_stats). Variant 1
+// gives an item to a warp. In both, the top-byte histogram is kept per warp in shared memory and
 // flushed to the global 256-bin histogram at the end, or earlier if a warp's
 // 32-bit bins could overflow. A lane keeps only its XOR in registers. The
 // item's top-byte sum is read off the warp's histogram: sum over bins of
@@ -76,10 +72,43 @@ __device__ __forceinline__ void finish_item(uint32_t x, uint32_t *h, int lane, u
     }
 }
 
+// Walks cnt consecutive counters of one key from Weyl term y: XOR of the
+// values into x, top-byte counts into the warp's histogram h. Round 1 is
+// carried by accumulation (t += e, e += c2: two additions per counter, no
+// per-block constants), B values per unrolled block.
+template <int B>
+__device__ __forceinline__ void walk_stats(uint64_t y, uint64_t key, uint64_t cnt, uint32_t &x, uint32_t *h) {
+    const uint64_t c2 = (key * key) << 1;
+    uint64_t t = round1_value(y);
+    uint64_t er = round1_delta(y, key);
+    uint64_t i = 0;
+    for (; i + B <= cnt; i += B) {
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            const uint64_t yn = add64(y, key);
+            const uint32_t u = squares32_tyz(t, y, yn);
+            y = yn;
+            t = add64(t, er);
+            er = add64(er, c2);
+            x ^= u;
+            atomicAdd(h + (u >> 24), 1u);
+        }
+    }
+    for (; i < cnt; ++i) {
+        const uint64_t yn = add64(y, key);
+        const uint32_t u = squares32_tyz(t, y, yn);
+        y = yn;
+        t = add64(t, er);
+        er = add64(er, c2);
+        x ^= u;
+        atomicAdd(h + (u >> 24), 1u);
+    }
+}
+
 // Variant 0: CTA items. Thread i of the block walks counters
 // [a + i * m, a + (i + 1) * m) of item [a, b), m = ceil((b - a) / block).
-// Two instantiations by block size: up to 256 threads the compiler keeps
-// about 63 registers (the fastest form measured), for 512 threads 54.
+// Two instantiations by block size (register targets for up to 256 and for
+// 512 threads).
 template <int B, int MAXB, int MINB>
 __global__ void __launch_bounds__(MAXB, MINB)
     fused_cta_kernel(const uint64_t *__restrict__ keys, const uint64_t *__restrict__ bases, uint64_t S,
@@ -101,36 +130,8 @@ __global__ void __launch_bounds__(MAXB, MINB)
         const uint64_t la = a + threadIdx.x * per_thread;
         const uint64_t lb = (la + per_thread < b) ? la + per_thread : b;
         const uint64_t key = keys[s];
-        const uint64_t c2 = (key * key) << 1;
-        uint64_t y = (bases[s] + la) * key;
-        uint64_t t = round1_value(y);  // round 1 by the recurrence of round1_delta
-        uint64_t er = round1_delta(y, key);
         uint32_t x = 0;
-        const uint64_t cnt = (lb > la) ? lb - la : 0;
-        // Blocks of B counters: t_{j+1} = t_j + e + j*c2 with e fixed for the
-        // block (one three-input addition per value), e += B*c2 per block.
-        uint64_t i = 0;
-        for (; i + B <= cnt; i += B) {
-#pragma unroll
-            for (int j = 0; j < B; ++j) {
-                const uint64_t yn = add64(y, key);
-                const uint32_t u = squares32_tyz(t, y, yn);
-                y = yn;
-                t = add64x3(t, er, c2 * static_cast<uint64_t>(j));
-                x ^= u;
-                atomicAdd(h + (u >> 24), 1u);
-            }
-            er = add64(er, c2 * B);
-        }
-        for (; i < cnt; ++i) {
-            const uint64_t yn = add64(y, key);
-            const uint32_t u = squares32_tyz(t, y, yn);
-            y = yn;
-            t = add64(t, er);
-            er = add64(er, c2);
-            x ^= u;
-            atomicAdd(h + (u >> 24), 1u);
-        }
+        walk_stats<B>((bases[s] + la) * key, key, (lb > la) ? lb - la : 0, x, h);
         finish_item(x, h, lane, s, b - a, weighted, since_flush, xor_out, sum_top, hist);
     }
     flush_hist(h, hist, lane);
@@ -160,40 +161,8 @@ __global__ void __launch_bounds__(512)
         const uint64_t la = a + lane * per_lane;
         const uint64_t lb = (la + per_lane < b) ? la + per_lane : b;
         const uint64_t key = __ldg(keys + s);
-        uint64_t y = (__ldg(bases + s) + la) * key;
-        uint64_t t = round1_value(y);  // round 1 by the recurrence of round1_delta
-        uint64_t er = round1_delta(y, key);
-        const uint64_t c2 = (key * key) << 1;
         uint32_t x = 0;
-        const uint64_t cnt = (lb > la) ? lb - la : 0;
-        // Blocks of 8 counters: t_{j+1} = t_j + e + j*c2 with e fixed for the
-        // block (one three-input addition per value), e += 8*c2 per block.
-        uint64_t jc2[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) jc2[j] = c2 * static_cast<uint64_t>(j);
-        const uint64_t c2x8 = c2 << 3;
-        uint64_t i = 0;
-        for (; i + 8 <= cnt; i += 8) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const uint64_t yn = add64(y, key);
-                const uint32_t u = squares32_tyz(t, y, yn);
-                y = yn;
-                t = add64x3(t, er, jc2[j]);
-                x ^= u;
-                atomicAdd(h + (u >> 24), 1u);
-            }
-            er = add64(er, c2x8);
-        }
-        for (; i < cnt; ++i) {
-            const uint64_t yn = add64(y, key);
-            const uint32_t u = squares32_tyz(t, y, yn);
-            y = yn;
-            t = add64(t, er);
-            er = add64(er, c2);
-            x ^= u;
-            atomicAdd(h + (u >> 24), 1u);
-        }
+        walk_stats<8>((__ldg(bases + s) + la) * key, key, (lb > la) ? lb - la : 0, x, h);
         finish_item(x, h, lane, s, b - a, weighted, since_flush, xor_out, sum_top, hist);
     }
     flush_hist(h, hist, lane);
