@@ -199,17 +199,50 @@ struct OpFill {
 
 // 53-bit double uniforms floor(squares64 / 2^11) * 2^-53, built with
 // integer operations only (see uniform53_bits).
+// 53-bit doubles. Per value the chunk takes the conversion's common path,
+// exact whenever v >= 2^43 (the upper word of v >> 11 is non-zero), and
+// flags the other values (probability 2^-21 each); when any active lane of
+// the warp flagged one, the flagged values are recomputed with the full
+// conversion. Keeping the rare path out of the per-value code matters: with
+// it inline, the compiler predicated it into every value (37.1 against 33.1
+// warp instructions per warp of outputs, 12 % slower).
+__device__ __forceinline__ uint64_t uniform53_bits_common(uint64_t v) {
+    const uint32_t kh = static_cast<uint32_t>(v >> 43);
+    const uint32_t kl = static_cast<uint32_t>(v >> 11);
+    const uint32_t pos = 31 - __clz(static_cast<int>(kh));  // 0..20 when kh != 0
+    const uint32_t sh = 20 - pos;
+    const uint32_t mhi = __funnelshift_l(kl, kh, sh);
+    const uint32_t mlo = kl << sh;
+    return (static_cast<uint64_t>(((1001u + pos) << 20) + mhi) << 32) | mlo;
+}
+
 struct OpUniformF64 {
     static constexpr int kHeadParity = 0;
     using T = double;
     static constexpr int EPC = 1;
     template <int W>
     __device__ static void chunk(uint64_t y, uint64_t e, uint64_t key, uint64_t c2, uint32_t (&w)[W]) {
+        uint32_t rare = 0;
         walk<W / 2>(y, e, key, c2, [&](int j, uint64_t t, uint64_t yy, uint64_t z) {
-            const uint64_t b = uniform53_bits(squares64_tyz(t, yy, z));
+            const uint64_t v = squares64_tyz(t, yy, z);
+            const uint64_t b = uniform53_bits_common(v);
+            rare |= static_cast<uint32_t>(v < (uint64_t{1} << 43)) << j;
             w[2 * j] = lo32(b);
             w[2 * j + 1] = hi32(b);
         });
+        // The vote covers the lanes still walking chunks (at the end of the
+        // vector region some lanes of a warp have finished theirs).
+        if (__any_sync(__activemask(), rare != 0u)) {
+#pragma unroll
+            for (int j = 0; j < W / 2; ++j) {
+                if (rare & (1u << j)) {
+                    const uint64_t yy = y + static_cast<uint64_t>(j) * key;
+                    const uint64_t b = uniform53_bits(squares64_yz(yy, add64(yy, key)));
+                    w[2 * j] = lo32(b);
+                    w[2 * j + 1] = hi32(b);
+                }
+            }
+        }
     }
     __device__ static T single(uint64_t ctr0, uint64_t key, uint64_t e) {
         return __longlong_as_double(static_cast<long long>(uniform53_bits(squares64(ctr0 + e, key))));

@@ -88,6 +88,31 @@ def test_uniform_f64(gpu_lib, n):
         assert np.array_equal(got.view(np.uint64), want), (n, off)
 
 
+def test_uniform_f64_rare_values_inside_chunks(gpu_lib):
+    """squares64 outputs below 2^43 (probability 2^-21 each) take the
+    conversion's rare path, which the vector kernels run after the chunk
+    when a lane flagged one: windows around such counters, found by
+    scanning the oracle, in every launch variant and block size, at two
+    output alignments, against the oracle."""
+    key = int(gpu_lib.make_keys(24, 1)[0])
+    v = oracle.fill64(key, 0, 1 << 24)
+    rare = np.nonzero(v < np.uint64(1 << 43))[0]
+    assert rare.size >= 2, rare.size
+    kid = C.SQ_KERNEL_UNIFORM_F64
+    try:
+        for r in rare[:3]:
+            base, n = int(r) - 3000, 6001
+            want = oracle.uniform_f64(key, base, n).view(np.uint64)
+            for variant in range(C.sq_num_variants(kid)):
+                for block in (128, 256, 512):
+                    C.sq_set_config(kid, 0, variant, block, 0)
+                    for off in (0, 1):
+                        got = _run(C.sq_uniform_f64, 8, np.float64, key, base, n=n, off=off)
+                        assert np.array_equal(got.view(np.uint64), want), (int(r), variant, block, off)
+    finally:
+        C.sq_set_config(kid, 0, 0, 256, 0)
+
+
 def test_uniform_f64_edge_integers(gpu_lib):
     """Outputs whose top bits are small exercise the exponent construction:
     found by scanning the oracle, then generated on the GPU one by one."""
