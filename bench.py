@@ -1005,15 +1005,18 @@ def profile_case(args):
         print(f"profile case {args.profile} streams={bt.nstreams} samples={bt.total} done",
               flush=True)
         return 0
+    set_n = 64 if args.profile == "batch" else n  # the batch case holds 64 streams
     if args.tune_file and os.path.exists(args.tune_file):
         # use the configuration tuned for the benchmark's size of this kernel
         C.sq_autotune_load(args.tune_file)
-        full = {"u32": N32, "u64": N64}.get(args.profile, 1 << 30)
+        # the benchmark's entry: by output count, for the batch by stream count
+        # (the 4096-stream workload's bucket, applied to this case's 64 streams)
+        full = {"u32": N32, "u64": N64, "batch": 4096}.get(args.profile, 1 << 30)
         c = C.sq_get_config(kids[args.profile], full)
-        C.sq_set_config(kids[args.profile], n, c.variant, c.block, c.ctas_per_sm)
+        C.sq_set_config(kids[args.profile], set_n, c.variant, c.block, c.ctas_per_sm)
     elif not args.no_tune:
         C.sq_autotune(kids[args.profile], n)
-    c = C.sq_get_config(kids[args.profile], n)
+    c = C.sq_get_config(kids[args.profile], set_n)
     print(f"profile config: {C.sq_variant_name(kids[args.profile], c.variant)} block {c.block} "
           f"ctas/SM {c.ctas_per_sm}", flush=True)
     if args.profile == "fused":
