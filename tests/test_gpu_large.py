@@ -112,6 +112,55 @@ def test_batch_stream_longer_than_2p32(gpu_lib):
     assert np.all(tail == CANARY)
 
 
+def test_flattened_warp_group_past_2p31(gpu_lib):
+    """The flattened-warp variants on a group of streams holding more than
+    2^31 values (one stream of 2^31 + 5000): the group scan runs in 64-bit
+    words, the per-position walk in 64-bit positions, and the segment
+    variant hands the group to that walk. Sampled outputs, windows at the
+    head, around 2^31 and the tail, the small streams in full, gaps and the
+    tail canary."""
+    import torch
+
+    keys = gpu_lib.make_keys(75, 5)
+    lengths = np.array([1000, (1 << 31) + 5000, 777, 0, 12345], dtype=np.int64)
+    gaps = np.array([3, 17, 5, 0, 64], dtype=np.int64)
+    offsets = np.zeros(5, dtype=np.int64)
+    pos = 0
+    for s in range(5):
+        pos += gaps[s]
+        offsets[s] = pos
+        pos += lengths[s]
+    n_out = pos + 11
+    bases = np.array([5, M64 - 1000, 0, 9, 1 << 40], dtype=np.uint64)
+    d_keys, d_bases, d_len, d_off = to_dev(keys), to_dev(bases), to_dev(lengths), to_dev(offsets)
+    names = {C.sq_variant_name(C.SQ_KERNEL_BATCH, v): v for v in range(C.sq_num_variants(C.SQ_KERNEL_BATCH))}
+    a, m = int(offsets[1]), int(lengths[1])
+    idx = workloads.sample_positions(m, 100_000, seed=76)
+    want_idx = oracle.pairs32(_ctrs(int(bases[1]), idx), keys[1])
+    try:
+        for name in ("flat-warp", "flat-seg8"):
+            C.sq_set_config(C.SQ_KERNEL_BATCH, 5, names[name], 128, 0)
+            out = filled_u32(n_out, CANARY)
+            C.sq_batch(d_keys.data_ptr(), d_bases.data_ptr(), d_len.data_ptr(), d_off.data_ptr(), 5,
+                       out.data_ptr(), stream_handle())
+            torch.cuda.synchronize()
+            for s in (0, 2, 4):
+                b0, k = int(offsets[s]), int(lengths[s])
+                got = out[b0 - int(gaps[s]):b0 + k].cpu().numpy().view(np.uint32)
+                assert np.all(got[:int(gaps[s])] == CANARY), (name, s)
+                assert np.array_equal(got[int(gaps[s]):], oracle.fill32(int(keys[s]), int(bases[s]), k)), (name, s)
+            assert np.array_equal(_at(out, idx + a).view(np.uint32), want_idx), name
+            for r in (0, (1 << 31) - 4096, m - (1 << 20)):
+                k = min(1 << 20, m - r)
+                got = out[a + r:a + r + k].cpu().numpy().view(np.uint32)
+                assert np.array_equal(got, oracle.fill32(int(keys[1]), (int(bases[1]) + r) & M64, k)), (name, r)
+            assert np.all(out[pos:].cpu().numpy().view(np.uint32) == CANARY), name
+            del out
+            torch.cuda.empty_cache()
+    finally:
+        C.sq_set_config(C.SQ_KERNEL_BATCH, 5, 0, 256, 0)
+
+
 def test_fused_more_than_2p32_counters_per_stream(gpu_lib):
     import torch
 
