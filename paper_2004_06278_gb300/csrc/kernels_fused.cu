@@ -179,8 +179,8 @@ const char *fused_variant_name(int variant) {
 namespace {
 const void *fused_fn(int variant, int block) {
     if (variant == 1) return reinterpret_cast<const void *>(&fused_kernel);
-    return block <= 256 ? reinterpret_cast<const void *>(&fused_cta_kernel<16, 256, 0>)
-                        : reinterpret_cast<const void *>(&fused_cta_kernel<16, 512, 2>);
+    return block <= 256 ? reinterpret_cast<const void *>(&fused_cta_kernel<32, 256, 0>)
+                        : reinterpret_cast<const void *>(&fused_cta_kernel<32, 512, 2>);
 }
 }  // namespace
 
@@ -220,10 +220,10 @@ cudaError_t launch_fused(const Cfg &cfg, const uint64_t *keys, const uint64_t *b
         fused_kernel<<<static_cast<unsigned>(grid), cfg.block, smem, stream>>>(
             keys, bases, nstreams, ctrs_per_stream, parts, part_len, xor_out, sum_top, hist256);
     else if (cfg.block <= 256)
-        fused_cta_kernel<16, 256, 0><<<static_cast<unsigned>(grid), cfg.block, smem, stream>>>(
+        fused_cta_kernel<32, 256, 0><<<static_cast<unsigned>(grid), cfg.block, smem, stream>>>(
             keys, bases, nstreams, ctrs_per_stream, parts, part_len, xor_out, sum_top, hist256);
     else
-        fused_cta_kernel<16, 512, 2><<<static_cast<unsigned>(grid), cfg.block, smem, stream>>>(
+        fused_cta_kernel<32, 512, 2><<<static_cast<unsigned>(grid), cfg.block, smem, stream>>>(
             keys, bases, nstreams, ctrs_per_stream, parts, part_len, xor_out, sum_top, hist256);
     return cudaGetLastError();
 }
