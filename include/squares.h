@@ -163,11 +163,12 @@ int sq_batch_validate(const int64_t *lengths, const int64_t *offsets, size_t nst
  *                  integers (so s keeps its relative accuracy as u1 -> 1),
  *                  atanh by its odd Taylor series to s^7; the angle is split
  *                  into an exact quadrant of lo and a remainder whose sine
- *                  and cosine come from Taylor series to t^9 / t^8; r from
- *                  the hardware reciprocal square root plus one Newton step.
+ *                  and cosine come from polynomials of degree 7 and 6
+ *                  fitted by least squares on Chebyshev nodes; r from the
+ *                  hardware reciprocal square root (r^2 times rsqrt(r^2)).
  *                  Error against the FP64 values, measured over all 2^32
- *                  values of each half: at most 7.5e-7 absolute where
- *                  |z| < 5 and 1.5e-7 relative beyond (bound stated for
+ *                  values of each half: at most 1.2e-6 absolute where
+ *                  |z| < 5 and 2.1e-7 relative beyond (bound stated for
  *                  callers: 2e-6 absolute, 1e-5 relative).
  *                  A pointer 4-byte but not 8-byte aligned still gets vector
  *                  stores: chunks then start at a pair's second element and
