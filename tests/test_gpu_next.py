@@ -48,8 +48,9 @@ def test_key_counter_mode(gpu_lib, ctr):
 @pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 8, 4097, 100_003])
 def test_key_counter_mode_alignments(gpu_lib, n):
     """Both launch paths of key-counter mode: keys and output 16-byte
-    aligned (for squares32 four keys per thread per step, then the n mod 4
-    tail) and either misaligned (one key per thread)."""
+    aligned (four keys per thread per step for squares32, then the n mod 4
+    tail; two for squares64, then an odd last key) and either misaligned
+    (one key per thread)."""
     import torch
 
     keys = gpu_lib.make_keys(26, n + 1)
