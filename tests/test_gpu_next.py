@@ -24,11 +24,14 @@ def _run(fn, elem, dtype, *args, n, off=0):
 def test_strided(gpu_lib, stride):
     key = int(gpu_lib.make_keys(21, 1)[0])
     base = M64 - 1000
-    for n in (1, 7, 1000, 300_001):
-        got32 = _run(C.sq_u32_strided, 4, np.uint32, key, base, stride, n=n, off=n % 3)
-        got64 = _run(C.sq_u64_strided, 8, np.uint64, key, base, stride, n=n, off=n % 2)
-        assert np.array_equal(got32, oracle.fill32_strided(key, base, stride, n)), (stride, n)
-        assert np.array_equal(got64, oracle.fill64_strided(key, base, stride, n)), (stride, n)
+    # around the vector paths' thresholds (1,024 squares32, 256 squares64
+    # outputs) and ragged tails of their 16- and 4-value chunks
+    for n in (1, 7, 255, 256, 1000, 1023, 1024, 1025, 4099, 300_001):
+        for off in {n % 4, 3}:
+            got32 = _run(C.sq_u32_strided, 4, np.uint32, key, base, stride, n=n, off=off)
+            got64 = _run(C.sq_u64_strided, 8, np.uint64, key, base, stride, n=n, off=off % 2)
+            assert np.array_equal(got32, oracle.fill32_strided(key, base, stride, n)), (stride, n, off)
+            assert np.array_equal(got64, oracle.fill64_strided(key, base, stride, n)), (stride, n, off)
 
 
 @pytest.mark.parametrize("ctr", [0, 1, 12345, M64])
