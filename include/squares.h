@@ -161,10 +161,11 @@ int sq_batch_validate(const int64_t *lengths, const int64_t *offsets, size_t nst
  *                  ln u1 = (E - 32) ln 2 + 2 atanh(s), s = D / (hi + 1 + 2^E)
  *                  where D = hi + 1 - 2^E is formed exactly in 32-bit
  *                  integers (so s keeps its relative accuracy as u1 -> 1),
- *                  atanh by its odd Taylor series to s^7; the angle is split
- *                  into an exact quadrant of lo and a remainder whose sine
- *                  and cosine come from polynomials of degree 7 and 6
- *                  fitted by least squares on Chebyshev nodes; r from the
+ *                  atanh by a fitted polynomial of degree 5; the angle is
+ *                  split into an exact quadrant of lo and a remainder whose
+ *                  sine and cosine come from polynomials of degree 7 and 6
+ *                  (all three fitted by least squares on Chebyshev nodes,
+ *                  csrc/fit_box_muller.py); r from the
  *                  hardware reciprocal square root (r^2 times rsqrt(r^2)).
  *                  Error against the FP64 values, measured over all 2^32
  *                  values of each half: at most 1.2e-6 absolute where
