@@ -116,22 +116,29 @@ def test_flattened_warp_group_past_2p31(gpu_lib):
     """The flattened-warp variants on a group of streams holding more than
     2^31 values (one stream of 2^31 + 5000): the group scan runs in 64-bit
     words, the per-position walk in 64-bit positions, and the segment
-    variant hands the group to that walk. Sampled outputs, windows at the
-    head, around 2^31 and the tail, the small streams in full, gaps and the
-    tail canary."""
+    variant hands the group to that walk; the next group, all short streams
+    past output 2^31, takes the segment walk there. Sampled outputs, windows
+    at the head, around 2^31 and the tail, the small streams in full, gaps
+    and the tail canary."""
     import torch
 
-    keys = gpu_lib.make_keys(75, 5)
-    lengths = np.array([1000, (1 << 31) + 5000, 777, 0, 12345], dtype=np.int64)
-    gaps = np.array([3, 17, 5, 0, 64], dtype=np.int64)
-    offsets = np.zeros(5, dtype=np.int64)
+    # streams 5..39 are short and follow the long one: the second group of
+    # 32 (streams 32..39) takes the segment walk at outputs past 2^31
+    S = 40
+    keys = gpu_lib.make_keys(75, S)
+    rng = np.random.default_rng(77)
+    lengths = np.concatenate([[1000, (1 << 31) + 5000, 777, 0, 12345],
+                              rng.integers(1, 300, S - 5)]).astype(np.int64)
+    gaps = np.concatenate([[3, 17, 5, 0, 64], rng.integers(0, 4, S - 5)]).astype(np.int64)
+    offsets = np.zeros(S, dtype=np.int64)
     pos = 0
-    for s in range(5):
+    for s in range(S):
         pos += gaps[s]
         offsets[s] = pos
         pos += lengths[s]
     n_out = pos + 11
-    bases = np.array([5, M64 - 1000, 0, 9, 1 << 40], dtype=np.uint64)
+    bases = np.concatenate([np.array([5, M64 - 1000, 0, 9, 1 << 40], dtype=np.uint64),
+                            rng.integers(0, 1 << 64, S - 5, dtype=np.uint64)])
     d_keys, d_bases, d_len, d_off = to_dev(keys), to_dev(bases), to_dev(lengths), to_dev(offsets)
     names = {C.sq_variant_name(C.SQ_KERNEL_BATCH, v): v for v in range(C.sq_num_variants(C.SQ_KERNEL_BATCH))}
     a, m = int(offsets[1]), int(lengths[1])
@@ -139,12 +146,12 @@ def test_flattened_warp_group_past_2p31(gpu_lib):
     want_idx = oracle.pairs32(_ctrs(int(bases[1]), idx), keys[1])
     try:
         for name in ("flat-warp", "flat-seg8"):
-            C.sq_set_config(C.SQ_KERNEL_BATCH, 5, names[name], 128, 0)
+            C.sq_set_config(C.SQ_KERNEL_BATCH, S, names[name], 128, 0)
             out = filled_u32(n_out, CANARY)
-            C.sq_batch(d_keys.data_ptr(), d_bases.data_ptr(), d_len.data_ptr(), d_off.data_ptr(), 5,
+            C.sq_batch(d_keys.data_ptr(), d_bases.data_ptr(), d_len.data_ptr(), d_off.data_ptr(), S,
                        out.data_ptr(), stream_handle())
             torch.cuda.synchronize()
-            for s in (0, 2, 4):
+            for s in [0, 2, 4] + list(range(5, S)):
                 b0, k = int(offsets[s]), int(lengths[s])
                 got = out[b0 - int(gaps[s]):b0 + k].cpu().numpy().view(np.uint32)
                 assert np.all(got[:int(gaps[s])] == CANARY), (name, s)
@@ -158,7 +165,7 @@ def test_flattened_warp_group_past_2p31(gpu_lib):
             del out
             torch.cuda.empty_cache()
     finally:
-        C.sq_set_config(C.SQ_KERNEL_BATCH, 5, 0, 256, 0)
+        C.sq_set_config(C.SQ_KERNEL_BATCH, S, 0, 256, 0)
 
 
 def test_fused_more_than_2p32_counters_per_stream(gpu_lib):
