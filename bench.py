@@ -417,8 +417,10 @@ def run_ours(args, rank, world, local):
             "avg_launch_ms": ms32,
             "peak_source": f"integer model: {sms} SMs x {LANES_PER_SM} lanes x {sm_max} MHz / "
                            f"{HEAVY_CYCLES_SQ32} FMA-heavy cycles per warp-sample = "
-                           f"{r_int32 / 1e9:.0f} Gsamples/s; hbm copy {hbm} GB/s ({peak_src}, "
-                           f"MEASURED_PEAKS.json); store-only ceiling: the best DRAM write rate measured here, "
+                           f"{r_int32 / 1e9:.0f} Gsamples/s; hbm copy {hbm} GB/s ("
+                           + ("measured, MEASURED_PEAKS.json" if peak_src == "measured"
+                              else "fallback figure: MEASURED_PEAKS.json absent")
+                           + f"); store-only ceiling: the best DRAM write rate measured here, "
                            f"of {store['configs']} sq_fill_u32 shapes and the squares64 launches",
             "limiter": "FMA-heavy pipe (ncu: busiest unit; the kernel without stores takes the "
                        "same time as with them)",
