@@ -148,9 +148,12 @@ def test_batch_equals_plain_per_stream(gpu_lib):
     torch.cuda.synchronize()
 
 
-def test_torch_graph_capture_and_replay(gpu_lib):
+@pytest.mark.parametrize("variant", ["st32", "flat-warp", "flat-seg8"])
+def test_torch_graph_capture_and_replay(gpu_lib, variant):
     """The launch is capture-safe: capture once, change lengths/offsets/bases
-    on the device, replay, and get the new batch."""
+    on the device, replay, and get the new batch; for the tile kernel and
+    for the flattened-warp kernels (whose grid follows the stream count,
+    known on the host)."""
     import torch
 
     b1 = workloads.small_ragged_batch(100, seed=31, max_len=10_000)
@@ -159,23 +162,29 @@ def test_torch_graph_capture_and_replay(gpu_lib):
     n_out = max(b1.total, b2.total) + 11
     keys, bases, lengths, offsets = _device_inputs(gpu_lib, b1)
     out = filled_u32(n_out, int(FILL))
-    s = torch.cuda.Stream()
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.stream(s):
-        gpu_lib.batch(keys, bases, lengths, offsets, out)  # warm-up outside capture
-        s.synchronize()
-        with torch.cuda.graph(g, stream=s):
-            gpu_lib.batch(keys, bases, lengths, offsets, out)
-    out.copy_(filled_u32(n_out, int(FILL)))
-    g.replay()
-    assert np.array_equal(host_u32(out), _expect(b1, n_out))
-    bases.copy_(to_dev(b2.bases))
-    lengths.copy_(to_dev(b2.lengths))
-    offsets.copy_(to_dev(b2.offsets))
-    out.copy_(filled_u32(n_out, int(FILL)))
-    for _ in range(3):
+    v = [i for i in range(C.sq_num_variants(C.SQ_KERNEL_BATCH))
+         if C.sq_variant_name(C.SQ_KERNEL_BATCH, i) == variant][0]
+    C.sq_set_config(C.SQ_KERNEL_BATCH, b1.nstreams, v, 128, 0)
+    try:
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            gpu_lib.batch(keys, bases, lengths, offsets, out)  # warm-up outside capture
+            s.synchronize()
+            with torch.cuda.graph(g, stream=s):
+                gpu_lib.batch(keys, bases, lengths, offsets, out)
+        out.copy_(filled_u32(n_out, int(FILL)))
         g.replay()
-    assert np.array_equal(host_u32(out), _expect(b2, n_out))
+        assert np.array_equal(host_u32(out), _expect(b1, n_out))
+        bases.copy_(to_dev(b2.bases))
+        lengths.copy_(to_dev(b2.lengths))
+        offsets.copy_(to_dev(b2.offsets))
+        out.copy_(filled_u32(n_out, int(FILL)))
+        for _ in range(3):
+            g.replay()
+        assert np.array_equal(host_u32(out), _expect(b2, n_out))
+    finally:
+        C.sq_set_config(C.SQ_KERNEL_BATCH, b1.nstreams, 0, 256, 0)
 
 
 def test_native_graph_helper(gpu_lib):
